@@ -1,0 +1,204 @@
+/*
+ * adft.h -- C ABI of the GB300 direct-SCF Coulomb/exchange (J/K) library.
+ *
+ * The library evaluates the Coulomb and exact-exchange matrices of Eq. 1
+ * (Sec. 1.2.1 of "Acceleration without Disruption: DFT Software as a
+ * Service", arXiv 2406.11185)
+ *
+ *     J_mn = sum_ls D_ls (mn|ls),        K_mn = sum_ls D_ls (ml|ns)
+ *
+ * (K without the hybrid factor c_x, which the caller applies) from
+ * four-centre electron-repulsion integrals over contracted Gaussian shells
+ * (the integral of the ERI paragraph of Sec. 1.2.2), computed directly on
+ * one GPU without density fitting.  Shell quartets are screened with the
+ * Cauchy-Schwarz bound S = Q_ab Q_cd and, in mixed precision, dispatched to
+ * FP32 or FP64 kernels by that bound (the mixed-precision bullet of Sec.
+ * 1.2.2).  The energy E_JK = 1/2 tr(DJ) - 1/4 tr(DK) and its nuclear gradient
+ * at fixed D are also provided.
+ *
+ * Conventions
+ *   - Units: bohr, hartree.
+ *   - A shell is (atom, l, exponents a_i, coefficients c_i).  The c_i multiply
+ *     normalised primitive Cartesian Gaussians
+ *        N(a,l) x^ax y^ay z^az exp(-a r^2),
+ *        N(a,l) = (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2l-1)!!),
+ *     the same N for every Cartesian component of the shell.  The library does
+ *     not renormalise contractions.
+ *   - Cartesian components are ordered by descending x power, then descending
+ *     y power (xx, xy, xz, yy, yz, zz).  Spherical components: p is (x, y, z);
+ *     l >= 2 is m = -l..l of the unit-norm real solid harmonics.
+ *   - Basis functions are ordered shell by shell in the order given to
+ *     adft_basis_create.  All matrices are row-major nbf x nbf float64.
+ *   - Schwarz bound: Q_ab = sqrt(max over Cartesian components mu in a,
+ *     nu in b of |(mu nu|mu nu)|).  A shell quartet is skipped iff
+ *     Q_ab Q_cd < thresh.  In mixed precision it runs in FP64 iff
+ *     Q_ab Q_cd >= split, else in FP32 with its contributions added into
+ *     FP64 accumulators.
+ *
+ * Memory and threads
+ *   - "dev" pointers are CUDA device pointers on the current device; "host"
+ *     pointers are ordinary host memory.  The caller owns every buffer it
+ *     passes.  The library owns the basis handle and the device workspace it
+ *     allocates at creation; nothing is allocated per J/K call.
+ *   - Every call that takes an adft_opts enqueues its work on opts->stream
+ *     (NULL = the legacy default stream) and returns without synchronising,
+ *     unless opts->check is 1 (see below) or a host output is requested.
+ *   - A handle may be used by one stream at a time.
+ *
+ * Errors: every function returns ADFT_OK (0) or a negative status; nothing
+ * aborts or traps.  adft_status_string() gives a description, and
+ * adft_last_error_message() the detail of the last failing call on this
+ * thread.
+ */
+#ifndef ADFT_H
+#define ADFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADFT_LMAX 3        /* highest shell angular momentum supported (f) */
+#define ADFT_MAX_NPRIM 16  /* highest number of primitives in one shell */
+
+enum {
+  ADFT_OK = 0,
+  ADFT_ERR_ARG = -1,          /* null pointer, bad size, l > ADFT_LMAX, nprim out of range, ... */
+  ADFT_ERR_UNSUPPORTED = -2,  /* valid request the library does not implement */
+  ADFT_ERR_ASYM_D = -3,       /* max|D - D^T| > 1e-12 max|D| (only with opts->check) */
+  ADFT_ERR_NONFINITE = -4,    /* D holds NaN or Inf (only with opts->check) */
+  ADFT_ERR_OOM = -5,          /* device or host allocation failed */
+  ADFT_ERR_CUDA = -6,         /* a CUDA runtime call failed */
+  ADFT_ERR_TIMEOUT = -7,      /* a bounded device-side wait ran out */
+  ADFT_ERR_ABORTED = -8       /* the abort flag of the handle was raised */
+};
+
+enum { ADFT_PREC_FP64 = 0, ADFT_PREC_MIXED = 1 };
+
+typedef struct adft_basis adft_basis; /* opaque, library-owned */
+typedef struct adft_batch adft_batch; /* opaque, library-owned */
+
+typedef struct {
+  int atom;             /* index into the atom array, 0 <= atom < natom */
+  int l;                /* angular momentum, 0 <= l <= ADFT_LMAX */
+  int nprim;            /* 1 <= nprim <= ADFT_MAX_NPRIM */
+  const double* exps;   /* host [nprim], > 0 */
+  const double* coefs;  /* host [nprim], coefficients of normalised primitives */
+} adft_shell;
+
+typedef struct {
+  double thresh;   /* Schwarz threshold (>= 0): skip iff Q_ab Q_cd < thresh */
+  double split;    /* ADFT_PREC_MIXED only: FP64 iff Q_ab Q_cd >= split */
+  int precision;   /* ADFT_PREC_FP64 or ADFT_PREC_MIXED */
+  int check;       /* 1: validate D on the device, synchronise the stream and
+                      return ADFT_ERR_ASYM_D / ADFT_ERR_NONFINITE; 0: no check,
+                      fully asynchronous */
+  void* stream;    /* cudaStream_t, NULL = legacy default stream */
+} adft_opts;
+
+/* Per-call statistics of the last J/K build (host copies). */
+typedef struct {
+  int64_t quartets_fp64;     /* shell quartets evaluated in FP64 */
+  int64_t quartets_fp32;     /* shell quartets evaluated in FP32 */
+  int64_t quartets_total;    /* unique shell quartets before screening */
+  int64_t prim_quartets_fp64; /* primitive quartets inside the FP64 ones */
+  int64_t prim_quartets_fp32; /* primitive quartets inside the FP32 ones */
+  double flops_fp64;         /* counted FP64 flops of the ERI + digestion kernels */
+  double flops_fp32;         /* counted FP32 flops of the ERI + digestion kernels */
+} adft_stats;
+
+/* Create a basis on the current CUDA device: copies the geometry and shells,
+ * builds the shell-pair data (Gaussian product centres, exponents and
+ * prefactors of every primitive pair, Sec. 1.2.2 "basis contractions ... as
+ * different shells": every shell is one segmented contraction), evaluates the
+ * Schwarz bounds Q_ab on the GPU and sorts the pairs of each
+ * angular-momentum class (l_a >= l_b) by descending Q (the angular-momentum
+ * reordering of Sec. 1.2.2).  Synchronous.
+ *   atom_xyz: host [natom*3] bohr.  shells: host [nshell].
+ *   spherical: 1 = spherical functions, 0 = Cartesian functions.
+ *   out: receives the handle; release it with adft_basis_destroy. */
+int adft_basis_create(const double* atom_xyz, int natom, const adft_shell* shells, int nshell,
+                      int spherical, adft_basis** out);
+
+/* Number of basis functions (spherical or Cartesian as created). */
+int adft_basis_nbf(const adft_basis* b, int* nbf);
+
+/* Number of atoms and shells. */
+int adft_basis_dims(const adft_basis* b, int* natom, int* nshell, int* ncart);
+
+/* Copy the Schwarz bounds to host memory: Q[a*(a+1)/2 + b] for shells
+ * a >= b in creation order.  Q: host [nshell*(nshell+1)/2]. */
+int adft_basis_schwarz(const adft_basis* b, double* Q);
+
+/* J and K of Eq. 1 for a symmetric density D.
+ *   D, J, K: dev [nbf*nbf] row-major float64; J and K are overwritten.
+ *   K is sum_ls D_ls (ml|ns) without c_x.  The result is symmetric to
+ *   round-off.  Statistics of the call are kept for adft_jk_last_stats. */
+int adft_jk_build(adft_basis* b, const double* D, const adft_opts* opts, double* J, double* K);
+
+/* E_JK = 1/2 tr(DJ) - 1/4 tr(DK).  Builds J and K internally (into the
+ * handle's workspace) and writes the energy.
+ *   E: dev pointer to one float64 if E_on_device = 1, else a host pointer
+ *   (then the call synchronises the stream). */
+int adft_jk_energy(adft_basis* b, const double* D, const adft_opts* opts, double* E, int E_on_device);
+
+/* Nuclear gradient dE_JK/dR at fixed D (derivative integrals contracted with
+ * G = 1/2 D(x)D - 1/8 (D(x)D exchange-permuted); quartets recomputed, none
+ * stored).  Screening and the precision bands use the undifferentiated
+ * bounds S = Q_ab Q_cd.
+ *   grad: dev [natom*3] float64, overwritten. */
+int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* opts, double* grad);
+
+/* Statistics of the last adft_jk_build / adft_jk_energy / adft_jk_grad on
+ * this handle (synchronises the handle's last stream). */
+int adft_jk_last_stats(adft_basis* b, adft_stats* st);
+
+/* Raise (1) or clear (0) the handle's abort flag.  A running or later build
+ * sees it on the device and returns ADFT_ERR_ABORTED (with opts->check = 1)
+ * or leaves a status readable by adft_jk_status. */
+int adft_basis_set_abort(adft_basis* b, int flag);
+
+/* Read the device status word of the handle (ADFT_OK or an error of the last
+ * asynchronous call); synchronises the handle's last stream. */
+int adft_jk_status(adft_basis* b);
+
+void adft_basis_destroy(adft_basis* b);
+
+/* ---- batched form: many molecules, one persistent launch per class ----- */
+
+/* Group existing bases (not copied; they must outlive the batch).
+ *   mols: host [nmol] handles, all created with the same `spherical`. */
+int adft_batch_create(adft_basis* const* mols, int nmol, adft_batch** out);
+
+/* Offsets (in float64 elements) of each molecule's nbf x nbf block in the
+ * packed matrices: offsets host [nmol+1], offsets[i+1]-offsets[i] = nbf_i^2. */
+int adft_batch_offsets(const adft_batch* bt, int64_t* offsets);
+
+/* Offsets of each molecule's natom x 3 gradient block: host [nmol+1]. */
+int adft_batch_grad_offsets(const adft_batch* bt, int64_t* offsets);
+
+/* J, K (and optionally E and the gradient) of every molecule with one
+ * persistent launch per angular-momentum class over a global quartet work
+ * list spanning all molecules.
+ *   D_packed, J_packed, K_packed: dev, packed per adft_batch_offsets.
+ *   E: dev [nmol] or NULL.  grad_packed: dev per adft_batch_grad_offsets or
+ *   NULL. */
+int adft_batch_jk(adft_batch* bt, const double* D_packed, const adft_opts* opts, double* J_packed,
+                  double* K_packed, double* E, double* grad_packed);
+
+void adft_batch_destroy(adft_batch* bt);
+
+/* ---- utilities ---------------------------------------------------------- */
+
+const char* adft_status_string(int status);
+const char* adft_last_error_message(void);
+
+/* Library version string. */
+const char* adft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADFT_H */

@@ -1,0 +1,233 @@
+"""Thin Python binding of the C ABI in include/adft.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``lib/libadft.so``; PyTorch only
+provides device memory and the current stream.  There is no CPU fallback: if
+the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libadft.so")
+
+ADFT_OK = 0
+ADFT_ERR_ARG = -1
+ADFT_ERR_UNSUPPORTED = -2
+ADFT_ERR_ASYM_D = -3
+ADFT_ERR_NONFINITE = -4
+ADFT_ERR_OOM = -5
+ADFT_ERR_CUDA = -6
+ADFT_ERR_TIMEOUT = -7
+ADFT_ERR_ABORTED = -8
+ADFT_PREC_FP64 = 0
+ADFT_PREC_MIXED = 1
+ADFT_LMAX = 3
+ADFT_MAX_NPRIM = 16
+
+EXPORTED = [
+    "adft_basis_create", "adft_basis_nbf", "adft_basis_dims", "adft_basis_schwarz", "adft_jk_build",
+    "adft_jk_energy", "adft_jk_grad", "adft_jk_last_stats", "adft_basis_set_abort", "adft_jk_status",
+    "adft_basis_destroy", "adft_batch_create", "adft_batch_offsets", "adft_batch_grad_offsets", "adft_batch_jk",
+    "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version",
+]
+
+
+class AdftError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status}) {detail}".strip())
+
+
+class adft_shell(ctypes.Structure):
+    _fields_ = [("atom", ctypes.c_int), ("l", ctypes.c_int), ("nprim", ctypes.c_int),
+                ("exps", ctypes.POINTER(ctypes.c_double)), ("coefs", ctypes.POINTER(ctypes.c_double))]
+
+
+class adft_opts(ctypes.Structure):
+    _fields_ = [("thresh", ctypes.c_double), ("split", ctypes.c_double), ("precision", ctypes.c_int),
+                ("check", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class adft_stats(ctypes.Structure):
+    _fields_ = [("quartets_fp64", ctypes.c_int64), ("quartets_fp32", ctypes.c_int64),
+                ("quartets_total", ctypes.c_int64), ("prim_quartets_fp64", ctypes.c_int64),
+                ("prim_quartets_fp32", ctypes.c_int64), ("flops_fp64", ctypes.c_double),
+                ("flops_fp32", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libadft.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_2406_11185_gb300/build.py)")
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    L.adft_basis_create.argtypes = [dp, ip, ctypes.POINTER(adft_shell), ip, ip, ctypes.POINTER(vp)]
+    L.adft_basis_nbf.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.adft_basis_dims.argtypes = [vp, ctypes.POINTER(ctypes.c_int)] * 1 + [ctypes.POINTER(ctypes.c_int)] * 3
+    L.adft_basis_schwarz.argtypes = [vp, dp]
+    L.adft_jk_build.argtypes = [vp, vp, ctypes.POINTER(adft_opts), vp, vp]
+    L.adft_jk_energy.argtypes = [vp, vp, ctypes.POINTER(adft_opts), vp, ip]
+    L.adft_jk_grad.argtypes = [vp, vp, ctypes.POINTER(adft_opts), vp]
+    L.adft_jk_last_stats.argtypes = [vp, ctypes.POINTER(adft_stats)]
+    L.adft_basis_set_abort.argtypes = [vp, ip]
+    L.adft_jk_status.argtypes = [vp]
+    L.adft_basis_destroy.argtypes = [vp]
+    L.adft_basis_destroy.restype = None
+    L.adft_batch_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
+    L.adft_batch_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.adft_batch_grad_offsets.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.adft_batch_jk.argtypes = [vp, vp, ctypes.POINTER(adft_opts), vp, vp, vp, vp]
+    L.adft_batch_destroy.argtypes = [vp]
+    L.adft_batch_destroy.restype = None
+    L.adft_status_string.argtypes = [ip]
+    L.adft_status_string.restype = ctypes.c_char_p
+    L.adft_last_error_message.restype = ctypes.c_char_p
+    L.adft_version.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def status_string(st: int) -> str:
+    return load().adft_status_string(int(st)).decode()
+
+
+def last_error() -> str:
+    return load().adft_last_error_message().decode()
+
+
+def _check(st: int, where: str):
+    if st != ADFT_OK:
+        raise AdftError(st, where, last_error())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_opts(thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None) -> adft_opts:
+    prec = {"fp64": ADFT_PREC_FP64, "mixed": ADFT_PREC_MIXED}[precision] if isinstance(precision, str) \
+        else int(precision)
+    return adft_opts(float(thresh), float(split), prec, 1 if check else 0, _stream_ptr(stream))
+
+
+class Basis:
+    """Owns one adft_basis handle (adft_basis_create / adft_basis_destroy)."""
+
+    def __init__(self, atoms, shells, spherical=True):
+        L = load()
+        self._keep = []
+        xyz = np.ascontiguousarray(np.asarray(atoms, dtype=np.float64).reshape(-1, 3))
+        arr = (adft_shell * len(shells))()
+        for i, (atom, l, exps, coefs) in enumerate(shells):
+            e = np.ascontiguousarray(exps, dtype=np.float64)
+            c = np.ascontiguousarray(coefs, dtype=np.float64)
+            self._keep += [e, c]
+            arr[i] = adft_shell(int(atom), int(l), len(e), e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        h = ctypes.c_void_p()
+        _check(L.adft_basis_create(xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), xyz.shape[0], arr,
+                                   len(shells), 1 if spherical else 0, ctypes.byref(h)), "adft_basis_create")
+        self.handle = h
+        self.natom = xyz.shape[0]
+        self.nshell = len(shells)
+        n = ctypes.c_int()
+        _check(L.adft_basis_nbf(h, ctypes.byref(n)), "adft_basis_nbf")
+        self.nbf = n.value
+        self._keep = None
+
+    @classmethod
+    def from_molecule(cls, mol):
+        return cls(mol.atoms, mol.shells, mol.spherical)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().adft_basis_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def schwarz(self) -> np.ndarray:
+        Q = np.zeros(self.nshell * (self.nshell + 1) // 2)
+        _check(load().adft_basis_schwarz(self.handle, Q.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "adft_basis_schwarz")
+        return Q
+
+
+def adft_basis_create(atoms, shells, spherical=True) -> Basis:
+    return Basis(atoms, shells, spherical)
+
+
+def _check_matrix(D, n):
+    import torch
+    if not (isinstance(D, torch.Tensor) and D.is_cuda and D.dtype == torch.float64 and D.is_contiguous()
+            and tuple(D.shape) == (n, n)):
+        raise ValueError(f"D must be a contiguous CUDA float64 tensor of shape ({n}, {n})")
+
+
+def adft_jk_build(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None, out=None):
+    """J, K (torch CUDA float64) of Eq. 1 for density D."""
+    import torch
+    _check_matrix(D, basis.nbf)
+    J, K = out if out is not None else (torch.empty_like(D), torch.empty_like(D))
+    o = make_opts(thresh, split, precision, check, stream)
+    _check(load().adft_jk_build(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
+                                ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(K.data_ptr())), "adft_jk_build")
+    return J, K
+
+
+def adft_jk_energy(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None,
+                   on_device=False):
+    """E_JK = 1/2 tr(DJ) - 1/4 tr(DK); a float, or a 1-element CUDA tensor."""
+    import torch
+    _check_matrix(D, basis.nbf)
+    o = make_opts(thresh, split, precision, check, stream)
+    if on_device:
+        E = torch.empty(1, dtype=torch.float64, device=D.device)
+        _check(load().adft_jk_energy(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
+                                     ctypes.c_void_p(E.data_ptr()), 1), "adft_jk_energy")
+        return E
+    e = ctypes.c_double()
+    _check(load().adft_jk_energy(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
+                                 ctypes.cast(ctypes.byref(e), ctypes.c_void_p), 0), "adft_jk_energy")
+    return e.value
+
+
+def adft_jk_grad(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None):
+    """dE_JK/dR [natom, 3] (torch CUDA float64) at fixed D."""
+    import torch
+    _check_matrix(D, basis.nbf)
+    g = torch.empty((basis.natom, 3), dtype=torch.float64, device=D.device)
+    o = make_opts(thresh, split, precision, check, stream)
+    _check(load().adft_jk_grad(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
+                               ctypes.c_void_p(g.data_ptr())), "adft_jk_grad")
+    return g
+
+
+def adft_jk_last_stats(basis: Basis) -> dict:
+    st = adft_stats()
+    _check(load().adft_jk_last_stats(basis.handle, ctypes.byref(st)), "adft_jk_last_stats")
+    return {k: getattr(st, k) for k, _ in adft_stats._fields_}
+
+
+def adft_basis_set_abort(basis: Basis, flag: bool):
+    _check(load().adft_basis_set_abort(basis.handle, 1 if flag else 0), "adft_basis_set_abort")
+
+
+def adft_jk_status(basis: Basis) -> int:
+    return int(load().adft_jk_status(basis.handle))

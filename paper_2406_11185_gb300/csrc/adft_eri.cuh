@@ -1,0 +1,877 @@
+// Device templates of the per-class ERI kernels (McMurchie-Davidson) with the
+// J/K digestion fused in.  Included by the per-precision translation units,
+// which instantiate one kernel per angular-momentum class pair
+// (la lb | lc ld), la >= lb, lc >= ld, (la,lb) >= (lc,ld): the
+// per-angular-momentum code paths of Sec. 1.2.2 ("GPU kernel code optimized
+// for each type of angular momentum"), generated here by the C++ compiler from
+// one template instead of a separate code generator.
+//
+// Integral scheme (Helgaker, Jorgensen, Olsen, "Molecular Electronic-Structure
+// Theory", Sec. 9.5 and 9.9): for primitive pairs p (bra) and q (ket)
+//   [ab|cd] = 2 pi^(5/2) / (p q sqrt(p+q)) K_p K_q
+//             sum_{tuv} E^ab_tuv sum_{tau nu phi} (-1)^(tau+nu+phi)
+//             E^cd_{tau nu phi} R_{t+tau, u+nu, v+phi}(alpha, P-Q)
+// evaluated as W_p[tuv][cd] = sum_q (ket transform) followed by one bra
+// transform per bra primitive, so the bra transform is amortised over the ket
+// primitives.  A thread owns one shell quartet and a chunk of CK ket
+// Cartesian components (all bra components), which bounds its state.
+#pragma once
+#include <utility>
+
+#include "adft_internal.cuh"
+
+namespace adft {
+
+// ---------------------------------------------------------------------------
+// small index helpers (all constexpr so that unrolled loops fold them)
+
+// Cartesian component k of a shell of angular momentum l -> powers (x, y, z),
+// ordered by descending x, then descending y.
+__host__ __device__ constexpr int cart_x(int l, int k) {
+  int i = l, off = 0;
+  while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
+  return i;
+}
+__host__ __device__ constexpr int cart_z(int l, int k) {
+  int i = l, off = 0;
+  while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
+  return k - off;
+}
+__host__ __device__ constexpr int cart_y(int l, int k) { return l - cart_x(l, k) - cart_z(l, k); }
+__host__ __device__ constexpr int cart_pow(int l, int k, int d) {
+  return d == 0 ? cart_x(l, k) : d == 1 ? cart_y(l, k) : cart_z(l, k);
+}
+
+// Hermite index (t, u, v), t + u + v <= L, ordered by n = t+u+v, then by
+// m = u+v, then by v: position = n(n+1)(n+2)/6 + m(m+1)/2 + v.
+__host__ __device__ constexpr int hidx(int t, int u, int v) {
+  return (t + u + v) * (t + u + v + 1) * (t + u + v + 2) / 6 + (u + v) * (u + v + 1) / 2 + v;
+}
+
+template <typename T> __device__ __forceinline__ T dload(const T* p) { return __ldg(p); }
+
+// chunk of ket components owned by one thread
+template <int NAB, int NHAB, int NCD, int BUDGET>
+struct ChunkPlan {
+  static constexpr int raw = BUDGET / (NAB + NHAB);
+  static constexpr int CK = raw < 1 ? 1 : (raw > NCD ? NCD : raw);
+  static constexpr int NCHUNK = (NCD + CK - 1) / CK;
+};
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static __device__ __forceinline__ const PrimPair<double>* pp(const BasisView& b) { return b.pp64; }
+  static constexpr int BUDGET = 640;
+};
+template <> struct Prec<float> {
+  static __device__ __forceinline__ const PrimPair<float>* pp(const BasisView& b) { return b.pp32; }
+  static constexpr int BUDGET = 640;
+};
+
+// ---------------------------------------------------------------------------
+// Boys function F_m(T) = int_0^1 t^2m exp(-T t^2) dt  (Helgaker Sec. 9.8.1).
+// FP64: 7-term Taylor expansion of F_L about the nearest tabulated point
+// (spacing 0.1, table built by the library's own series code), then downward
+// recursion F_m = (2T F_{m+1} + e^-T)/(2m+1); for T >= 60 the closed form
+// F_0 = sqrt(pi/T)/2 (erf(sqrt T) = 1 to double precision) and upward
+// recursion F_{m+1} = ((2m+1) F_m - e^-T)/(2T).
+template <int L>
+__device__ __forceinline__ void boys_fp64(double T, const double* __restrict__ tab, double* F) {
+  if (T < BOYS_TMAX) {
+    const int i = __double2int_rn(T * (1.0 / BOYS_H));
+    const double y = i * BOYS_H - T;
+    const double* row = tab + i * (BOYS_MMAX + 1) + L;
+    double acc = __ldg(row + 6);
+#pragma unroll
+    for (int k = 6; k >= 1; --k) acc = __ldg(row + k - 1) + acc * (y * (1.0 / k));
+    const double e = exp(-T);
+    F[L] = acc;
+#pragma unroll
+    for (int m = L - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + e) * (1.0 / (2 * m + 1));
+  } else {
+    const double r = 1.0 / T;
+    const double e = exp(-T);
+    F[0] = 0.88622692545275801365 * sqrt(r);
+#pragma unroll
+    for (int m = 0; m < L; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * (0.5 * r);
+  }
+}
+
+// FP32, scaled: G_m = c^m F_m(T) with c = max(1, 2T), so that G_m stays in
+// range for any T (the caller rescales the Hermite integrals accordingly).
+// 5-term Taylor expansion below T = 60; above, the asymptotic recursion
+// G_{m+1} = (2m+1) G_m whose neglected e^-T term is below 1e-10 relative.
+template <int L>
+__device__ __forceinline__ void boys_fp32_scaled(float T, const float* __restrict__ tab, float* G) {
+  if (T < (float)BOYS_TMAX) {
+    const int i = __float2int_rn(T * (float)(1.0 / BOYS_H));
+    const float y = i * (float)BOYS_H - T;
+    const float* row = tab + i * (BOYS_MMAX + 1) + L;
+    float acc = __ldg(row + 4);
+#pragma unroll
+    for (int k = 4; k >= 1; --k) acc = __ldg(row + k - 1) + acc * (y * (1.0f / k));
+    const float e = __expf(-T);
+    float F[L + 1];
+    F[L] = acc;
+#pragma unroll
+    for (int m = L - 1; m >= 0; --m) F[m] = (2.0f * T * F[m + 1] + e) * (1.0f / (2 * m + 1));
+    const float c = fmaxf(1.0f, 2.0f * T);
+    float cn = 1.0f;
+#pragma unroll
+    for (int m = 0; m <= L; ++m) { G[m] = F[m] * cn; cn *= c; }
+  } else {
+    G[0] = 0.88622692545f * rsqrtf(T);
+#pragma unroll
+    for (int m = 0; m < L; ++m) G[m + 1] = (2 * m + 1) * G[m];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Hermite expansion coefficients of one direction (Helgaker eqs. 9.5.6-9.5.7),
+// without the exp(-mu X_AB^2) factor (it lives in the pair prefactor K):
+// E[(i*(LB+1)+j)*(LA+LB+1)+t], i <= LA, j <= LB, t <= i+j.
+template <typename T, int LA, int LB>
+__device__ __forceinline__ void hermite_E(T PA, T PB, T o2p, T* E) {
+  constexpr int NT = LA + LB + 1;
+#pragma unroll
+  for (int x = 0; x < (LA + 1) * (LB + 1) * NT; ++x) E[x] = T(0);
+  E[0] = T(1);
+#pragma unroll
+  for (int i = 1; i <= LA; ++i)
+#pragma unroll
+    for (int t = 0; t <= i; ++t) {
+      T v = PA * ((t <= i - 1) ? E[((i - 1) * (LB + 1)) * NT + t] : T(0));
+      if (t > 0) v += o2p * E[((i - 1) * (LB + 1)) * NT + t - 1];
+      if (t + 1 <= i - 1) v += T(t + 1) * E[((i - 1) * (LB + 1)) * NT + t + 1];
+      E[(i * (LB + 1)) * NT + t] = v;
+    }
+#pragma unroll
+  for (int i = 0; i <= LA; ++i)
+#pragma unroll
+    for (int j = 1; j <= LB; ++j)
+#pragma unroll
+      for (int t = 0; t <= i + j; ++t) {
+        const int src = (i * (LB + 1) + j - 1) * NT;
+        T v = PB * ((t <= i + j - 1) ? E[src + t] : T(0));
+        if (t > 0) v += o2p * E[src + t - 1];
+        if (t + 1 <= i + j - 1) v += T(t + 1) * E[src + t + 1];
+        E[(i * (LB + 1) + j) * NT + t] = v;
+      }
+}
+
+// Hermite Coulomb integrals R_tuv, t+u+v <= L (Helgaker eqs. 9.9.18-9.9.20),
+// from the base values B_n = R^n_000, raised in t, u or v from layer n+1.
+template <typename T, int L>
+__device__ __forceinline__ void hermite_R(const T* B, T X, T Y, T Z, T* R) {
+  T tmp[nherm(L)];
+#pragma unroll
+  for (int n = L; n >= 0; --n) {
+    // layer n goes to R when (L - n) is even, else to tmp; layer n+1 is in the other
+    T* dst = ((L - n) % 2 == 0) ? R : tmp;
+    const T* src = ((L - n) % 2 == 0) ? tmp : R;
+#pragma unroll
+    for (int t = 0; t <= L - n; ++t)
+#pragma unroll
+      for (int u = 0; u <= L - n - t; ++u)
+#pragma unroll
+        for (int v = 0; v <= L - n - t - u; ++v) {
+          T val;
+          if (t == 0 && u == 0 && v == 0) {
+            val = B[n];
+          } else if (t > 0) {
+            val = X * src[hidx(t - 1, u, v)];
+            if (t > 1) val += T(t - 1) * src[hidx(t - 2, u, v)];
+          } else if (u > 0) {
+            val = Y * src[hidx(t, u - 1, v)];
+            if (u > 1) val += T(u - 1) * src[hidx(t, u - 2, v)];
+          } else {
+            val = Z * src[hidx(t, u, v - 1)];
+            if (v > 1) val += T(v - 1) * src[hidx(t, u, v - 2)];
+          }
+          dst[hidx(t, u, v)] = val;
+        }
+  }
+  if constexpr (L % 2 == 1) {
+    // layer 0 landed in tmp
+#pragma unroll
+    for (int x = 0; x < nherm(L); ++x) R[x] = tmp[x];
+  }
+}
+
+// Base values R^n_000 and the Hermite integrals of one primitive quartet.
+// FP64: B_n = (-2 alpha)^n F_n(T), R as defined.
+// FP32: with c = max(1, 2T), s^2 = 2 alpha / c: B_n = (-c)^n F_n c^0... i.e.
+// B_n = (-1)^n G_n, coordinates scaled by s, and R_tuv = s^(t+u+v) Rs_tuv,
+// which keeps every intermediate in single-precision range.
+template <typename T, int L>
+__device__ __forceinline__ void prim_R(T alpha, T X, T Y, T Z, const BasisView& bv, T* R) {
+  T B[L + 1];
+  const T Tb = alpha * (X * X + Y * Y + Z * Z);
+  if constexpr (sizeof(T) == 8) {
+    boys_fp64<L>(Tb, bv.boys64, B);
+    T f = -2.0 * alpha, pw = f;
+#pragma unroll
+    for (int n = 1; n <= L; ++n) { B[n] *= pw; pw *= f; }
+    hermite_R<T, L>(B, X, Y, Z, R);
+  } else {
+    boys_fp32_scaled<L>(Tb, bv.boys32, B);
+#pragma unroll
+    for (int n = 1; n <= L; n += 2) B[n] = -B[n];
+    const float c = fmaxf(1.0f, 2.0f * Tb);
+    const float s = sqrtf(2.0f * alpha / c);
+    hermite_R<T, L>(B, X * s, Y * s, Z * s, R);
+    float sp = s;
+#pragma unroll
+    for (int n = 1; n <= L; ++n) {
+#pragma unroll
+      for (int x = nherm(n - 1); x < nherm(n); ++x) R[x] *= sp;
+      sp *= s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Contracted Cartesian block of one shell quartet for the ket components
+// [chunk*CK, chunk*CK + CK): G[ab*CK + k] = (a b | c d)_k.
+template <typename T, int LA, int LB, int LC, int LD, int CK>
+__device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int ket, int chunk, T* G) {
+  constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+  constexpr int NAB = NA * NB, NCD = NC * ND;
+  constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+  constexpr int NHAB = nherm(LAB);
+  constexpr int EA = (LA + 1) * (LB + 1) * (LAB + 1), EC = (LC + 1) * (LD + 1) * (LCD + 1);
+  constexpr int NTA = LAB + 1, NTC = LCD + 1;
+  const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
+
+  const int off0 = __ldg(bv.pair_pp_off + bra), n0 = __ldg(bv.pair_pp_n + bra);
+  const int off1 = __ldg(bv.pair_pp_off + ket), n1 = __ldg(bv.pair_pp_n + ket);
+  const T ABx = (T)__ldg(bv.pair_AB + 3 * bra), ABy = (T)__ldg(bv.pair_AB + 3 * bra + 1),
+          ABz = (T)__ldg(bv.pair_AB + 3 * bra + 2);
+  const T CDx = (T)__ldg(bv.pair_AB + 3 * ket), CDy = (T)__ldg(bv.pair_AB + 3 * ket + 1),
+          CDz = (T)__ldg(bv.pair_AB + 3 * ket + 2);
+
+  // powers of the owned ket components
+  int cp[CK][6];
+#pragma unroll
+  for (int k = 0; k < CK; ++k) {
+    int kc = chunk * CK + k;
+    if (kc >= NCD) kc = NCD - 1;  // padded slot, never digested
+    const int ic = kc / ND, id = kc % ND;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) { cp[k][d] = cart_pow(LC, ic, d); cp[k][3 + d] = cart_pow(LD, id, d); }
+  }
+
+#pragma unroll
+  for (int x = 0; x < NAB * CK; ++x) G[x] = T(0);
+
+  for (int ip = 0; ip < n0; ++ip) {
+    const PrimPair<T> bp = pp[off0 + ip];
+    const T o2p = T(0.5) / bp.p;
+    T Eab[3][EA];
+    hermite_E<T, LA, LB>(bp.PAx, bp.PAx + ABx, o2p, Eab[0]);
+    hermite_E<T, LA, LB>(bp.PAy, bp.PAy + ABy, o2p, Eab[1]);
+    hermite_E<T, LA, LB>(bp.PAz, bp.PAz + ABz, o2p, Eab[2]);
+
+    T W[NHAB * CK];
+#pragma unroll
+    for (int x = 0; x < NHAB * CK; ++x) W[x] = T(0);
+
+    for (int iq = 0; iq < n1; ++iq) {
+      const PrimPair<T> kq = pp[off1 + iq];
+      const T o2q = T(0.5) / kq.p;
+      T Ecd[3][EC];
+      hermite_E<T, LC, LD>(kq.PAx, kq.PAx + CDx, o2q, Ecd[0]);
+      hermite_E<T, LC, LD>(kq.PAy, kq.PAy + CDy, o2q, Ecd[1]);
+      hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CDz, o2q, Ecd[2]);
+      const T p = bp.p, q = kq.p, pq = p + q;
+      const T alpha = p * q / pq;
+      T R[nherm(L)];
+      prim_R<T, L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
+      // 2 pi^(5/2) = 34.98683665524972
+      const T pref = T(34.98683665524972) * kq.K / (p * q * sqrt(pq));
+#pragma unroll
+      for (int k = 0; k < CK; ++k) {
+        const int cx = cp[k][0], cy = cp[k][1], cz = cp[k][2], dx = cp[k][3], dy = cp[k][4], dz = cp[k][5];
+        for (int tau = 0; tau <= cx + dx; ++tau) {
+          const T ex = Ecd[0][(cx * (LD + 1) + dx) * NTC + tau];
+          for (int nu = 0; nu <= cy + dy; ++nu) {
+            const T exy = ex * Ecd[1][(cy * (LD + 1) + dy) * NTC + nu];
+            for (int phi = 0; phi <= cz + dz; ++phi) {
+              T e2 = pref * exy * Ecd[2][(cz * (LD + 1) + dz) * NTC + phi];
+              if ((tau + nu + phi) & 1) e2 = -e2;
+              // all bra Hermite functions (t,u,v), t+u+v <= LAB
+#pragma unroll
+              for (int n = 0; n <= LAB; ++n)
+#pragma unroll
+                for (int m = 0; m <= n; ++m)
+#pragma unroll
+                  for (int v = 0; v <= m; ++v) {
+                    const int t = n - m, u = m - v;
+                    W[hidx(t, u, v) * CK + k] += e2 * R[hidx(t + tau, u + nu, v + phi)];
+                  }
+            }
+          }
+        }
+      }
+    }
+    // bra transform of this bra primitive
+#pragma unroll
+    for (int ab = 0; ab < NAB; ++ab) {
+      const int ia = ab / NB, ib = ab % NB;
+      const int ax = cart_pow(LA, ia, 0), ay = cart_pow(LA, ia, 1), az = cart_pow(LA, ia, 2);
+      const int bx = cart_pow(LB, ib, 0), by = cart_pow(LB, ib, 1), bz = cart_pow(LB, ib, 2);
+#pragma unroll
+      for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+        for (int u = 0; u <= ay + by; ++u)
+#pragma unroll
+          for (int v = 0; v <= az + bz; ++v) {
+            const T e1 = bp.K * Eab[0][(ax * (LB + 1) + bx) * NTA + t] * Eab[1][(ay * (LB + 1) + by) * NTA + u] *
+                         Eab[2][(az * (LB + 1) + bz) * NTA + v];
+#pragma unroll
+            for (int k = 0; k < CK; ++k) G[ab * CK + k] += e1 * W[hidx(t, u, v) * CK + k];
+          }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Runtime-L versions for the larger classes: one compiled kernel per
+// precision serves every class with L > 4, with state in thread-local arrays
+// sized for f shells (plus one derivative order).
+
+constexpr int GEN_LMAX = LMAX + 1;                       // shells incl. derivative
+constexpr int GEN_L = 4 * LMAX + 1;                      // largest total L
+constexpr int GEN_NH = nherm(GEN_L);
+constexpr int GEN_E = (GEN_LMAX + 1) * (LMAX + 1) * (GEN_LMAX + LMAX + 1);
+constexpr int GEN_BUDGET = 640;
+
+__device__ __forceinline__ int hidx_rt(int t, int u, int v) {
+  const int n = t + u + v, m = u + v;
+  return n * (n + 1) * (n + 2) / 6 + m * (m + 1) / 2 + v;
+}
+// position of the component (x, y, l-x-y) in the Cartesian order of shell l
+__device__ __forceinline__ int cart_index_dev(int l, int x, int y) {
+  const int d = l - x;  // components with larger x come first
+  return d * (d + 1) / 2 + (d - y);
+}
+__device__ __forceinline__ void cart_pows_rt(int l, int k, int& x, int& y, int& z) {
+  int i = l, off = 0;
+  while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
+  x = i; z = k - off; y = l - x - z;
+}
+
+template <typename T>
+__device__ __forceinline__ void hermite_E_rt(int LA, int LB, T PA, T PB, T o2p, T* E) {
+  const int NT = LA + LB + 1;
+  for (int x = 0; x < (LA + 1) * (LB + 1) * NT; ++x) E[x] = T(0);
+  E[0] = T(1);
+#pragma unroll 1
+  for (int i = 1; i <= LA; ++i)
+#pragma unroll 1
+    for (int t = 0; t <= i; ++t) {
+      const int src = ((i - 1) * (LB + 1)) * NT;
+      T v = (t <= i - 1) ? PA * E[src + t] : T(0);
+      if (t > 0) v += o2p * E[src + t - 1];
+      if (t + 1 <= i - 1) v += T(t + 1) * E[src + t + 1];
+      E[(i * (LB + 1)) * NT + t] = v;
+    }
+#pragma unroll 1
+  for (int i = 0; i <= LA; ++i)
+#pragma unroll 1
+    for (int j = 1; j <= LB; ++j)
+#pragma unroll 1
+      for (int t = 0; t <= i + j; ++t) {
+        const int src = (i * (LB + 1) + j - 1) * NT;
+        T v = (t <= i + j - 1) ? PB * E[src + t] : T(0);
+        if (t > 0) v += o2p * E[src + t - 1];
+        if (t + 1 <= i + j - 1) v += T(t + 1) * E[src + t + 1];
+        E[(i * (LB + 1) + j) * NT + t] = v;
+      }
+}
+
+__device__ __forceinline__ void boys_fp64_rt(int L, double T, const double* __restrict__ tab, double* F) {
+  if (T < BOYS_TMAX) {
+    const int i = __double2int_rn(T * (1.0 / BOYS_H));
+    const double y = i * BOYS_H - T;
+    const double* row = tab + i * (BOYS_MMAX + 1) + L;
+    double acc = __ldg(row + 6);
+#pragma unroll
+    for (int k = 6; k >= 1; --k) acc = __ldg(row + k - 1) + acc * (y * (1.0 / k));
+    const double e = exp(-T);
+    F[L] = acc;
+#pragma unroll 1
+    for (int m = L - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + e) / (2 * m + 1);
+  } else {
+    const double r = 1.0 / T;
+    const double e = exp(-T);
+    F[0] = 0.88622692545275801365 * sqrt(r);
+#pragma unroll 1
+    for (int m = 0; m < L; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * (0.5 * r);
+  }
+}
+
+__device__ __forceinline__ void boys_fp32_scaled_rt(int L, float T, const float* __restrict__ tab, float* G) {
+  if (T < (float)BOYS_TMAX) {
+    const int i = __float2int_rn(T * (float)(1.0 / BOYS_H));
+    const float y = i * (float)BOYS_H - T;
+    const float* row = tab + i * (BOYS_MMAX + 1) + L;
+    float acc = __ldg(row + 4);
+#pragma unroll
+    for (int k = 4; k >= 1; --k) acc = __ldg(row + k - 1) + acc * (y * (1.0f / k));
+    const float e = __expf(-T);
+    G[L] = acc;
+#pragma unroll 1
+    for (int m = L - 1; m >= 0; --m) G[m] = (2.0f * T * G[m + 1] + e) / (float)(2 * m + 1);
+    const float c = fmaxf(1.0f, 2.0f * T);
+    float cn = c;
+#pragma unroll 1
+    for (int m = 1; m <= L; ++m) { G[m] *= cn; cn *= c; }
+  } else {
+    G[0] = 0.88622692545f * rsqrtf(T);
+#pragma unroll 1
+    for (int m = 0; m < L; ++m) G[m + 1] = (2 * m + 1) * G[m];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void hermite_R_rt(int L, const T* B, T X, T Y, T Z, T* R, T* tmp) {
+#pragma unroll 1
+  for (int n = L; n >= 0; --n) {
+    T* dst = ((L - n) % 2 == 0) ? R : tmp;
+    const T* src = ((L - n) % 2 == 0) ? tmp : R;
+#pragma unroll 1
+    for (int t = 0; t <= L - n; ++t)
+#pragma unroll 1
+      for (int u = 0; u <= L - n - t; ++u)
+#pragma unroll 1
+        for (int v = 0; v <= L - n - t - u; ++v) {
+          T val;
+          if (t == 0 && u == 0 && v == 0) {
+            val = B[n];
+          } else if (t > 0) {
+            val = X * src[hidx_rt(t - 1, u, v)];
+            if (t > 1) val += T(t - 1) * src[hidx_rt(t - 2, u, v)];
+          } else if (u > 0) {
+            val = Y * src[hidx_rt(t, u - 1, v)];
+            if (u > 1) val += T(u - 1) * src[hidx_rt(t, u - 2, v)];
+          } else {
+            val = Z * src[hidx_rt(t, u, v - 1)];
+            if (v > 1) val += T(v - 1) * src[hidx_rt(t, u, v - 2)];
+          }
+          dst[hidx_rt(t, u, v)] = val;
+        }
+  }
+  if (L % 2 == 1) {
+    const int nh = (L + 1) * (L + 2) * (L + 3) / 6;
+    for (int x = 0; x < nh; ++x) R[x] = tmp[x];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void prim_R_rt(int L, T alpha, T X, T Y, T Z, const BasisView& bv, T* R, T* tmp) {
+  T B[GEN_L + 1];
+  const T Tb = alpha * (X * X + Y * Y + Z * Z);
+  if constexpr (sizeof(T) == 8) {
+    boys_fp64_rt(L, Tb, bv.boys64, B);
+    const T f = -2.0 * alpha;
+    T pw = f;
+#pragma unroll 1
+    for (int n = 1; n <= L; ++n) { B[n] *= pw; pw *= f; }
+    hermite_R_rt<T>(L, B, X, Y, Z, R, tmp);
+  } else {
+    boys_fp32_scaled_rt(L, Tb, bv.boys32, B);
+#pragma unroll 1
+    for (int n = 1; n <= L; n += 2) B[n] = -B[n];
+    const float c = fmaxf(1.0f, 2.0f * Tb);
+    const float s = sqrtf(2.0f * alpha / c);
+    hermite_R_rt<T>(L, B, X * s, Y * s, Z * s, R, tmp);
+    float sp = s;
+#pragma unroll 1
+    for (int n = 1; n <= L; ++n) {
+      const int lo = n * (n + 1) * (n + 2) / 6, hi = (n + 1) * (n + 2) * (n + 3) / 6;
+      for (int x = lo; x < hi; ++x) R[x] *= sp;
+      sp *= s;
+    }
+  }
+}
+
+// Runtime class description.
+struct RtClass {
+  int la, lb, lc, ld, ck, nchunk;
+};
+
+__host__ __device__ inline RtClass make_rt_class(int la, int lb, int lc, int ld) {
+  RtClass c{la, lb, lc, ld, 1, 1};
+  const int nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
+  const int raw = GEN_BUDGET / (nab + nherm(la + lb));
+  c.ck = raw < 1 ? 1 : (raw > ncd ? ncd : raw);
+  c.nchunk = (ncd + c.ck - 1) / c.ck;
+  return c;
+}
+
+template <typename T>
+__device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView& bv, int bra, int ket, int chunk,
+                                              T* G, const T* __restrict__ bra_w = nullptr) {
+  const int LA = C.la, LB = C.lb, LC = C.lc, LD = C.ld, CK = C.ck;
+  const int NB = ncart(LB), ND = ncart(LD);
+  const int NAB = ncart(LA) * NB, NCD = ncart(LC) * ND;
+  const int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+  const int NTA = LAB + 1, NTC = LCD + 1;
+  const int EA = (LA + 1) * (LB + 1) * NTA, EC = (LC + 1) * (LD + 1) * NTC;
+  const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
+  const int off0 = __ldg(bv.pair_pp_off + bra), n0 = __ldg(bv.pair_pp_n + bra);
+  const int off1 = __ldg(bv.pair_pp_off + ket), n1 = __ldg(bv.pair_pp_n + ket);
+  const T ABx = (T)__ldg(bv.pair_AB + 3 * bra), ABy = (T)__ldg(bv.pair_AB + 3 * bra + 1),
+          ABz = (T)__ldg(bv.pair_AB + 3 * bra + 2);
+  const T CDx = (T)__ldg(bv.pair_AB + 3 * ket), CDy = (T)__ldg(bv.pair_AB + 3 * ket + 1),
+          CDz = (T)__ldg(bv.pair_AB + 3 * ket + 2);
+  const int nhab = nherm(LAB);
+  const int kc0 = chunk * CK;
+  const int nk = min(CK, NCD - kc0);
+
+  T Eab[3 * GEN_E], Ecd[3 * GEN_E];
+  T R[GEN_NH], tmp[GEN_NH];
+  T W[GEN_BUDGET];
+  for (int x = 0; x < NAB * CK; ++x) G[x] = T(0);
+
+#pragma unroll 1
+  for (int ip = 0; ip < n0; ++ip) {
+    const PrimPair<T> bp = pp[off0 + ip];
+    const T o2p = T(0.5) / bp.p;
+    hermite_E_rt<T>(LA, LB, bp.PAx, bp.PAx + ABx, o2p, Eab);
+    hermite_E_rt<T>(LA, LB, bp.PAy, bp.PAy + ABy, o2p, Eab + EA);
+    hermite_E_rt<T>(LA, LB, bp.PAz, bp.PAz + ABz, o2p, Eab + 2 * EA);
+    for (int x = 0; x < nhab * CK; ++x) W[x] = T(0);
+#pragma unroll 1
+    for (int iq = 0; iq < n1; ++iq) {
+      const PrimPair<T> kq = pp[off1 + iq];
+      const T o2q = T(0.5) / kq.p;
+      hermite_E_rt<T>(LC, LD, kq.PAx, kq.PAx + CDx, o2q, Ecd);
+      hermite_E_rt<T>(LC, LD, kq.PAy, kq.PAy + CDy, o2q, Ecd + EC);
+      hermite_E_rt<T>(LC, LD, kq.PAz, kq.PAz + CDz, o2q, Ecd + 2 * EC);
+      const T p = bp.p, q = kq.p, pq = p + q;
+      const T alpha = p * q / pq;
+      prim_R_rt<T>(L, alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R, tmp);
+      const T pref = T(34.98683665524972) * kq.K / (p * q * sqrt(pq));
+#pragma unroll 1
+      for (int k = 0; k < nk; ++k) {
+        const int kc = kc0 + k;
+        int cx, cy, cz, dx, dy, dz;
+        cart_pows_rt(LC, kc / ND, cx, cy, cz);
+        cart_pows_rt(LD, kc % ND, dx, dy, dz);
+#pragma unroll 1
+        for (int tau = 0; tau <= cx + dx; ++tau) {
+          const T ex = Ecd[(cx * (LD + 1) + dx) * NTC + tau];
+#pragma unroll 1
+          for (int nu = 0; nu <= cy + dy; ++nu) {
+            const T exy = ex * Ecd[EC + (cy * (LD + 1) + dy) * NTC + nu];
+#pragma unroll 1
+            for (int phi = 0; phi <= cz + dz; ++phi) {
+              T e2 = pref * exy * Ecd[2 * EC + (cz * (LD + 1) + dz) * NTC + phi];
+              if ((tau + nu + phi) & 1) e2 = -e2;
+              int h = 0;
+#pragma unroll 1
+              for (int n = 0; n <= LAB; ++n)
+#pragma unroll 1
+                for (int m = 0; m <= n; ++m)
+#pragma unroll 4
+                  for (int v = 0; v <= m; ++v, ++h) {
+                    const int t = n - m, u = m - v;
+                    W[h * CK + k] += e2 * R[hidx_rt(t + tau, u + nu, v + phi)];
+                  }
+            }
+          }
+        }
+      }
+    }
+    const T Kw = bra_w ? bp.K * bra_w[off0 + ip] : bp.K;
+#pragma unroll 1
+    for (int ab = 0; ab < NAB; ++ab) {
+      int ax, ay, az, bx, by, bz;
+      cart_pows_rt(LA, ab / NB, ax, ay, az);
+      cart_pows_rt(LB, ab % NB, bx, by, bz);
+#pragma unroll 1
+      for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll 1
+        for (int u = 0; u <= ay + by; ++u)
+#pragma unroll 1
+          for (int v = 0; v <= az + bz; ++v) {
+            const T e1 = Kw * Eab[(ax * (LB + 1) + bx) * NTA + t] * Eab[EA + (ay * (LB + 1) + by) * NTA + u] *
+                         Eab[2 * EA + (az * (LB + 1) + bz) * NTA + v];
+            const int h = hidx_rt(t, u, v);
+            for (int k = 0; k < nk; ++k) G[ab * CK + k] += e1 * W[h * CK + k];
+          }
+    }
+  }
+}
+
+template <typename T>
+__device__ __noinline__ void digest_rt(const RtClass& C, const JKLaunch& a, int bra, int ket, int chunk,
+                                       const T* G) {
+  const int NA = ncart(C.la), NB = ncart(C.lb), ND = ncart(C.ld);
+  const int NCD = ncart(C.lc) * ND, CK = C.ck;
+  const BasisView& bv = a.bv;
+  const int sa = __ldg(bv.pair_a + bra), sb = __ldg(bv.pair_b + bra);
+  const int sc = __ldg(bv.pair_a + ket), sd = __ldg(bv.pair_b + ket);
+  const int oa = __ldg(bv.shell_coff + sa), ob = __ldg(bv.shell_coff + sb);
+  const int oc = __ldg(bv.shell_coff + sc), od = __ldg(bv.shell_coff + sd);
+  const long n = bv.ncart;
+  T w = T(1);
+  if (sa == sb) w *= T(0.5);
+  if (sc == sd) w *= T(0.5);
+  if (a.same_class && bra == ket) w *= T(0.5);
+  const T w4 = T(4) * w, w2 = T(2) * w;
+  const T* __restrict__ D = nullptr;
+  if constexpr (sizeof(T) == 8) D = (const T*)a.D64; else D = (const T*)a.D32;
+  const int kc0 = chunk * CK, nk = min(CK, NCD - kc0);
+#pragma unroll 1
+  for (int ab = 0; ab < NA * NB; ++ab) {
+    T s = T(0);
+    for (int k = 0; k < nk; ++k) {
+      const int kc = kc0 + k;
+      s += G[ab * CK + k] * dload(D + (oc + kc / ND) * n + od + kc % ND);
+    }
+    atomicAdd(a.J + (oa + ab / NB) * n + ob + ab % NB, (double)(w4 * s));
+  }
+#pragma unroll 1
+  for (int k = 0; k < nk; ++k) {
+    const int kc = kc0 + k, ic = kc / ND, id = kc % ND;
+    T s = T(0);
+    for (int ab = 0; ab < NA * NB; ++ab) s += G[ab * CK + k] * dload(D + (oa + ab / NB) * n + ob + ab % NB);
+    atomicAdd(a.J + (oc + ic) * n + od + id, (double)(w4 * s));
+#pragma unroll 1
+    for (int ia = 0; ia < NA; ++ia) {
+      T s_ac = T(0), s_ad = T(0);
+      for (int ib = 0; ib < NB; ++ib) {
+        const T g = G[(ia * NB + ib) * CK + k];
+        s_ac += g * dload(D + (ob + ib) * n + od + id);
+        s_ad += g * dload(D + (ob + ib) * n + oc + ic);
+      }
+      atomicAdd(a.K + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
+      atomicAdd(a.K + (oa + ia) * n + od + id, (double)(w2 * s_ad));
+    }
+#pragma unroll 1
+    for (int ib = 0; ib < NB; ++ib) {
+      T s_bc = T(0), s_bd = T(0);
+      for (int ia = 0; ia < NA; ++ia) {
+        const T g = G[(ia * NB + ib) * CK + k];
+        s_bc += g * dload(D + (oa + ia) * n + od + id);
+        s_bd += g * dload(D + (oa + ia) * n + oc + ic);
+      }
+      atomicAdd(a.K + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
+      atomicAdd(a.K + (ob + ib) * n + od + id, (double)(w2 * s_bd));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// work decoding: quartet index -> (bra, ket) by binary search over the
+// per-bra prefix of kept kets (the implicit class-sorted work list).
+__device__ __forceinline__ void decode_quartet(const JKLaunch& a, long long qi, int& bra, int& ket) {
+  int lo = 0, hi = a.nbra;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(a.prefix + mid) <= qi) lo = mid; else hi = mid;
+  }
+  long long j = qi - __ldg(a.prefix + lo);
+  if (a.ket_start) j += __ldg(a.ket_start + lo);
+  bra = a.bra_first + lo;
+  ket = a.ket_first + (int)j;
+}
+
+// J/K digestion of one quartet block (Cartesian, unsymmetrised accumulators):
+// with w = s_ab s_cd s_(ab,cd) (1/2 for each coincidence)
+//   J_mn += 4w sum_ls g D_ls,   J_ls += 4w sum_mn g D_mn,
+//   K_ml += 2w sum_ns g D_ns,   K_nl += 2w sum_ms g D_ms,
+//   K_ms += 2w sum_nl g D_nl,   K_ns += 2w sum_ml g D_ml,
+// which after X <- (X + X^T)/2 equals the sum over all 8 index permutations.
+template <typename T, int LA, int LB, int LC, int LD, int CK>
+__device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int chunk, const T* G) {
+  constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+  constexpr int NCD = NC * ND;
+  const BasisView& bv = a.bv;
+  const int sa = __ldg(bv.pair_a + bra), sb = __ldg(bv.pair_b + bra);
+  const int sc = __ldg(bv.pair_a + ket), sd = __ldg(bv.pair_b + ket);
+  const int oa = __ldg(bv.shell_coff + sa), ob = __ldg(bv.shell_coff + sb);
+  const int oc = __ldg(bv.shell_coff + sc), od = __ldg(bv.shell_coff + sd);
+  const long n = bv.ncart;
+  T w = T(1);
+  if (sa == sb) w *= T(0.5);
+  if (sc == sd) w *= T(0.5);
+  if (a.same_class && bra == ket) w *= T(0.5);
+  const T w4 = T(4) * w, w2 = T(2) * w;
+  const T* __restrict__ D = nullptr;
+  if constexpr (sizeof(T) == 8) D = (const T*)a.D64; else D = (const T*)a.D32;
+
+  // J_ab += 4w sum_cd g D_cd
+  T Dcd[CK];
+#pragma unroll
+  for (int k = 0; k < CK; ++k) {
+    const int kc = chunk * CK + k;
+    Dcd[k] = (kc < NCD) ? dload(D + (oc + kc / ND) * n + od + kc % ND) : T(0);
+  }
+#pragma unroll
+  for (int ia = 0; ia < NA; ++ia)
+#pragma unroll
+    for (int ib = 0; ib < NB; ++ib) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < CK; ++k) s += G[(ia * NB + ib) * CK + k] * Dcd[k];
+      atomicAdd(a.J + (oa + ia) * n + ob + ib, (double)(w4 * s));
+    }
+  // J_cd += 4w sum_ab g D_ab
+#pragma unroll
+  for (int k = 0; k < CK; ++k) {
+    const int kc = chunk * CK + k;
+    if (kc >= NCD) break;
+    T s = T(0);
+#pragma unroll
+    for (int ia = 0; ia < NA; ++ia)
+#pragma unroll
+      for (int ib = 0; ib < NB; ++ib) s += G[(ia * NB + ib) * CK + k] * dload(D + (oa + ia) * n + ob + ib);
+    atomicAdd(a.J + (oc + kc / ND) * n + od + kc % ND, (double)(w4 * s));
+  }
+  // K contributions
+#pragma unroll
+  for (int k = 0; k < CK; ++k) {
+    const int kc = chunk * CK + k;
+    if (kc >= NCD) break;
+    const int ic = kc / ND, id = kc % ND;
+#pragma unroll
+    for (int ia = 0; ia < NA; ++ia) {
+      T s_ac = T(0), s_ad = T(0);
+#pragma unroll
+      for (int ib = 0; ib < NB; ++ib) {
+        const T g = G[(ia * NB + ib) * CK + k];
+        s_ac += g * dload(D + (ob + ib) * n + od + id);
+        s_ad += g * dload(D + (ob + ib) * n + oc + ic);
+      }
+      atomicAdd(a.K + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
+      atomicAdd(a.K + (oa + ia) * n + od + id, (double)(w2 * s_ad));
+    }
+#pragma unroll
+    for (int ib = 0; ib < NB; ++ib) {
+      T s_bc = T(0), s_bd = T(0);
+#pragma unroll
+      for (int ia = 0; ia < NA; ++ia) {
+        const T g = G[(ia * NB + ib) * CK + k];
+        s_bc += g * dload(D + (oa + ia) * n + od + id);
+        s_bd += g * dload(D + (oa + ia) * n + oc + ic);
+      }
+      atomicAdd(a.K + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
+      atomicAdd(a.K + (ob + ib) * n + od + id, (double)(w2 * s_bd));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent J/K kernel of one class pair and one precision band.  Warps take
+// 32 work items at a time from a device atomic counter (the single-GPU form of
+// the dynamically scheduled global task counter of Sec. 1.2.2); an item is a
+// (quartet, ket chunk).  No thread ever waits on another.
+constexpr int JK_THREADS = 128;
+
+// Classes small enough to keep every intermediate in registers get a fully
+// unrolled instantiation; the rest use the runtime-L kernel.
+__host__ __device__ constexpr bool is_small_class(int la, int lb, int lc, int ld) {
+  return la + lb + lc + ld <= 4 && ncart(la) * ncart(lb) * ncart(lc) * ncart(ld) <= 81;
+}
+
+template <typename T, int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
+  constexpr int NAB = ncart(LA) * ncart(LB), NCD = ncart(LC) * ncart(LD);
+  using Plan = ChunkPlan<NAB, nherm(LA + LB), NCD, Prec<T>::BUDGET>;
+  constexpr int CK = Plan::CK, NCHUNK = Plan::NCHUNK;
+  const long long total = (long long)__ldg(a.prefix + a.nbra) * NCHUNK;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.counter, 32ULL);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= total) break;
+    if (*(volatile const int*)a.abort_flag) {
+      if (lane == 0) atomicCAS(a.status, 0, ADFT_ERR_ABORTED);
+      break;
+    }
+    const long long item = (long long)base + lane;
+    if (item < total) {
+      const long long qi = item / NCHUNK;
+      const int chunk = (int)(item - qi * NCHUNK);
+      int bra, ket;
+      decode_quartet(a, qi, bra, ket);
+      T G[NAB * CK];
+      quartet_block<T, LA, LB, LC, LD, CK>(a.bv, bra, ket, chunk, G);
+      digest<T, LA, LB, LC, LD, CK>(a, bra, ket, chunk, G);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a, RtClass C) {
+  const long long total = (long long)__ldg(a.prefix + a.nbra) * C.nchunk;
+  const int lane = threadIdx.x & 31;
+  T G[GEN_BUDGET];
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.counter, 32ULL);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= total) break;
+    if (*(volatile const int*)a.abort_flag) {
+      if (lane == 0) atomicCAS(a.status, 0, ADFT_ERR_ABORTED);
+      break;
+    }
+    const long long item = (long long)base + lane;
+    if (item < total) {
+      const long long qi = item / C.nchunk;
+      const int chunk = (int)(item - qi * C.nchunk);
+      int bra, ket;
+      decode_quartet(a, qi, bra, ket);
+      quartet_block_rt<T>(C, a.bv, bra, ket, chunk, G);
+      digest_rt<T>(C, a, bra, ket, chunk, G);
+    }
+  }
+}
+
+// Schwarz bounds of the pairs of one class: Q = sqrt(max |(mn|mn)|), FP64.
+static __global__ void __launch_bounds__(JK_THREADS) k_schwarz_generic(BasisView bv, RtClass C, int first, int n,
+                                                                 double* Q) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int pr = first + i;
+  const int NAB = ncart(C.la) * ncart(C.lb);
+  double mx = 0.0;
+  double G[GEN_BUDGET];
+  for (int chunk = 0; chunk < C.nchunk; ++chunk) {
+    quartet_block_rt<double>(C, bv, pr, pr, chunk, G);
+    for (int k = 0; k < C.ck; ++k) {
+      const int kc = chunk * C.ck + k;
+      if (kc < NAB) mx = fmax(mx, fabs(G[kc * C.ck + k]));
+    }
+  }
+  Q[pr] = sqrt(mx);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch tables: one launcher per (X, Y) class pair, X >= Y
+template <typename T, int X, int Y>
+cudaError_t launch_one(const JKLaunch& a, int grid, cudaStream_t s) {
+  constexpr int LA = cls_la(X), LB = cls_lb(X), LC = cls_la(Y), LD = cls_lb(Y);
+  if constexpr (X >= Y && is_small_class(LA, LB, LC, LD)) {
+    k_jk<T, LA, LB, LC, LD><<<grid, JK_THREADS, 0, s>>>(a);
+  } else {
+    k_jk_generic<T><<<grid, JK_THREADS, 0, s>>>(a, make_rt_class(LA, LB, LC, LD));
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int... I>
+cudaError_t dispatch_jk(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s,
+                        std::integer_sequence<int, I...>) {
+  using Fn = cudaError_t (*)(const JKLaunch&, int, cudaStream_t);
+  static constexpr Fn table[] = {&launch_one<T, I / NCLS, I % NCLS>...};
+  if (X < 0 || Y < 0 || X >= NCLS || Y > X) return cudaErrorInvalidValue;
+  return table[X * NCLS + Y](a, grid, s);
+}
+
+}  // namespace adft

@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of the GB300 J/K
+// library.  Nothing here is part of the public C ABI (include/adft.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "adft.h"
+
+namespace adft {
+
+constexpr int LMAX = ADFT_LMAX;               // shells up to f
+constexpr int NCLS = (LMAX + 1) * (LMAX + 2) / 2;  // pair classes (la >= lb)
+constexpr int NCP = NCLS * (NCLS + 1) / 2;    // class pairs (X >= Y)
+constexpr int LTOT = 4 * LMAX + 1;            // largest L incl. one derivative
+constexpr int BOYS_MMAX = LTOT + 8;           // table columns
+constexpr double BOYS_H = 0.1;                // table spacing in T
+constexpr int BOYS_NT = 601;                  // T = 0 .. 60
+constexpr double BOYS_TMAX = 60.0;            // beyond: asymptotic / upward
+
+__host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ constexpr int cls_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
+__host__ __device__ constexpr int cls_la(int X) {
+  return X < 1 ? 0 : X < 3 ? 1 : X < 6 ? 2 : X < 10 ? 3 : 4;
+}
+__host__ __device__ constexpr int cls_lb(int X) { return X - cls_la(X) * (cls_la(X) + 1) / 2; }
+__host__ __device__ constexpr int cp_index(int X, int Y) { return X * (X + 1) / 2 + Y; }
+
+// Primitive-pair record (8 values): Gaussian product centre P, exponent sum p,
+// P - A, and K = c_a c_b exp(-a b / p |A-B|^2) (normalised-primitive
+// coefficients included).  P - B = (P - A) + (A - B).
+template <typename T>
+struct alignas(sizeof(T) * 8) PrimPair {
+  T Px, Py, Pz, p, PAx, PAy, PAz, K;
+};
+
+// Device view of one basis (all arrays on the device).
+struct BasisView {
+  int nshell, natom, ncart, nbf, spherical;
+  const int* shell_l;
+  const int* shell_atom;
+  const int* shell_coff;   // first Cartesian function of each shell
+  const double* xyz;       // [natom][3]
+  int npair;
+  const int* pair_a;       // shell with the larger l (ties: larger index)
+  const int* pair_b;
+  const double* pair_Q;    // Schwarz bound
+  const int* pair_pp_off;  // first primitive pair
+  const int* pair_pp_n;    // number of primitive pairs
+  const double* pair_AB;   // [npair][3] A - B
+  const PrimPair<double>* pp64;
+  const PrimPair<float>* pp32;
+  const double* boys64;    // [BOYS_NT][BOYS_MMAX+1] F_m(i h)
+  const float* boys32;
+  const double* pp_w64;    // [2][npp]: 2 a and 2 b of every primitive pair
+  const float* pp_w32;
+  long long npp;
+};
+
+// One class-pair launch of the J/K kernel.
+struct JKLaunch {
+  BasisView bv;
+  int bra_first, nbra;      // pairs of class X: [bra_first, bra_first + nbra)
+  int ket_first;            // pairs of class Y start here
+  int same_class;           // X == Y
+  const long long* prefix;  // [nbra + 1] quartets before each bra
+  const int* ket_start;     // [nbra] first ket of the band (NULL: 0)
+  unsigned long long* counter;  // dynamic work counter (zeroed)
+  const double* D64;        // Cartesian D [ncart][ncart]
+  const float* D32;
+  double* J;                // Cartesian accumulators (unsymmetrised)
+  double* K;
+  const int* abort_flag;    // device flag polled between work chunks
+  int* status;              // device status word
+};
+
+struct GradLaunch {
+  JKLaunch jk;
+  double* grad;             // [natom][3]
+};
+
+// Launchers implemented in the per-precision translation units.
+cudaError_t launch_jk_fp64(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
+cudaError_t launch_jk_fp32(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
+cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
+cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
+cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s);
+// Boys tables in device memory of the current device (built once).
+cudaError_t boys_tables(const double** t64, const float** t32);
+
+// Counted flops of one primitive quartet / one contracted quartet of a class
+// (used only for reporting).
+double class_flops_prim(int X, int Y);
+double class_flops_quartet(int X, int Y);
+
+void set_error(const std::string& msg);
+
+}  // namespace adft

@@ -232,47 +232,54 @@ def _sph_matrix(l: int) -> np.ndarray:
 
 
 def overlap_matrix(mol: Molecule, spherical: bool | None = None) -> np.ndarray:
-    """AO overlap matrix by Gauss-Hermite quadrature of each 1-D factor."""
+    """AO overlap matrix by Gauss-Hermite quadrature of each 1-D factor,
+    vectorised over all shell pairs with the same (l_a, l_b, nprim_a, nprim_b)."""
     sph = mol.spherical if spherical is None else spherical
     gh_x, gh_w = np.polynomial.hermite.hermgauss(8)  # exact to degree 15
-    offs = []
-    o = 0
+    offs, o = [], 0
     for _, l, _, _ in mol.shells:
         offs.append(o)
         o += nsph(l) if sph else ncart(l)
     S = np.zeros((o, o))
-    for ia, (atA, la, ea, ca) in enumerate(mol.shells):
-        A = mol.atoms[atA]
-        na_ = nsph(la) if sph else ncart(la)
+    groups: dict = {}
+    for ia, (_, la, ea, _) in enumerate(mol.shells):
         for ib in range(ia + 1):
-            atB, lb, eb, cb = mol.shells[ib]
-            B = mol.atoms[atB]
-            a = ea[:, None]
-            b = eb[None, :]
+            lb, eb = mol.shells[ib][1], mol.shells[ib][2]
+            groups.setdefault((la, lb, len(ea), len(eb)), []).append((ia, ib))
+    sphm = {l: _sph_matrix(l) for l in range(5)}
+    for (la, lb, na, nb), pairs in groups.items():
+        pairs = np.array(pairs)
+        for c0 in range(0, len(pairs), 4096):
+            pr = pairs[c0:c0 + 4096]
+            A = mol.atoms[[mol.shells[i][0] for i in pr[:, 0]]][:, None, None, :]
+            B = mol.atoms[[mol.shells[i][0] for i in pr[:, 1]]][:, None, None, :]
+            a = np.array([mol.shells[i][2] for i in pr[:, 0]])[:, :, None]
+            b = np.array([mol.shells[i][2] for i in pr[:, 1]])[:, None, :]
+            ca = np.array([mol.shells[i][3] for i in pr[:, 0]])[:, :, None]
+            cb = np.array([mol.shells[i][3] for i in pr[:, 1]])[:, None, :]
             p = a + b
             P = (a[..., None] * A + b[..., None] * B) / p[..., None]
-            pref = np.exp(-(a * b / p) * np.sum((A - B) ** 2))
+            pref = np.exp(-(a * b / p) * np.sum((A - B) ** 2, axis=-1))
             norm_a = (2 * a / np.pi) ** 0.75 * (4 * a) ** (la / 2) / math.sqrt(_dfact(2 * la - 1))
             norm_b = (2 * b / np.pi) ** 0.75 * (4 * b) ** (lb / 2) / math.sqrt(_dfact(2 * lb - 1))
-            w = ca[:, None] * cb[None, :] * norm_a * norm_b * pref * (np.pi / p) ** 1.5
-            # 1-D moments M[d][i][j] = (1/sqrt(pi)) sum_k w_k (x_k/sqrt(p) + P - A)^i (.. - B)^j
-            x = gh_x[None, None, :] / np.sqrt(p)[..., None]
+            w = ca * cb * norm_a * norm_b * pref * (np.pi / p) ** 1.5
+            x = gh_x / np.sqrt(p)[..., None]
             M = np.zeros((3, la + 1, lb + 1) + p.shape)
             for d in range(3):
-                xa = x + (P[..., d] - A[d])[..., None]
-                xb = x + (P[..., d] - B[d])[..., None]
+                xa = x + (P[..., d] - A[..., d])[..., None]
+                xb = x + (P[..., d] - B[..., d])[..., None]
                 for i in range(la + 1):
                     for j in range(lb + 1):
                         M[d, i, j] = np.sum(gh_w * xa ** i * xb ** j, axis=-1) / math.sqrt(math.pi)
-            blk = np.zeros((ncart(la), ncart(lb)))
+            blk = np.zeros((len(pr), ncart(la), ncart(lb)))
             for ka, (ax, ay, az) in enumerate(cart_powers(la)):
                 for kb, (bx, by, bz) in enumerate(cart_powers(lb)):
-                    blk[ka, kb] = np.sum(w * M[0, ax, bx] * M[1, ay, by] * M[2, az, bz])
+                    blk[:, ka, kb] = np.sum(w * M[0, ax, bx] * M[1, ay, by] * M[2, az, bz], axis=(1, 2))
             if sph:
-                blk = _sph_matrix(la) @ blk @ _sph_matrix(lb).T
-            nb_ = blk.shape[1]
-            S[offs[ia]:offs[ia] + na_, offs[ib]:offs[ib] + nb_] = blk
-            S[offs[ib]:offs[ib] + nb_, offs[ia]:offs[ia] + na_] = blk.T
+                blk = np.einsum("mi,pij,nj->pmn", sphm[la], blk, sphm[lb])
+            for (ia, ib), bl in zip(pr, blk):
+                S[offs[ia]:offs[ia] + bl.shape[0], offs[ib]:offs[ib] + bl.shape[1]] = bl
+                S[offs[ib]:offs[ib] + bl.shape[1], offs[ia]:offs[ia] + bl.shape[0]] = bl.T
     return S
 
 

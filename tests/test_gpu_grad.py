@@ -1,0 +1,61 @@
+"""GPU nuclear gradient of E_JK against the oracle's analytic gradient,
+central finite differences of the GPU energy (h = 1e-4 bohr, <= 1e-6 Eh/bohr)
+and the zero net force of translation invariance."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2406_11185_gb300 import adft, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(name):
+    mol, opt = synth.config(name)
+    D = synth.make_density(mol, synth.default_nocc(mol, opt["nocc"]), opt["dseed"])
+    return mol, opt, D
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_f"])
+def test_grad_fp64_vs_oracle(name):
+    mol, opt, D = _case(name)
+    b = adft.Basis.from_molecule(mol)
+    g = adft.adft_jk_grad(b, torch.from_numpy(D).cuda(), thresh=opt["thresh"]).cpu().numpy()
+    gr = oracle.grad(mol, D, opt["thresh"])
+    print(f"{name}: max|dgrad|={np.max(np.abs(g - gr)):.2e} max|grad|={np.max(np.abs(gr)):.2e} "
+          f"net={np.max(np.abs(g.sum(0))):.2e}")
+    assert np.max(np.abs(g - gr)) <= 1e-9
+    assert np.max(np.abs(g.sum(axis=0))) <= 1e-10 * max(1.0, np.max(np.abs(g)))
+
+
+def test_grad_vs_finite_differences_of_gpu_energy():
+    mol, opt, D = _case("small")
+    Dt = torch.from_numpy(D).cuda()
+    b = adft.Basis.from_molecule(mol)
+    g = adft.adft_jk_grad(b, Dt, thresh=opt["thresh"]).cpu().numpy()
+    h = 1e-4
+    rng = np.random.default_rng(4)
+    coords = [(int(rng.integers(mol.natom)), int(rng.integers(3))) for _ in range(6)]
+    for a, k in coords:
+        e = []
+        for sgn in (1, -1):
+            x = mol.atoms.copy()
+            x[a, k] += sgn * h
+            bb = adft.Basis.from_molecule(mol.with_atoms(x))
+            e.append(adft.adft_jk_energy(bb, Dt, thresh=opt["thresh"]))
+        fd = (e[0] - e[1]) / (2 * h)
+        assert abs(fd - g[a, k]) <= 1e-6, (a, k, fd, g[a, k])
+    assert np.max(np.abs(g.sum(axis=0))) <= 1e-10 * max(1.0, np.max(np.abs(g)))
+
+
+def test_grad_mixed_error_reported():
+    mol, opt, D = _case("small")
+    b = adft.Basis.from_molecule(mol)
+    Dt = torch.from_numpy(D).cuda()
+    g64 = adft.adft_jk_grad(b, Dt, thresh=opt["thresh"]).cpu().numpy()
+    gmx = adft.adft_jk_grad(b, Dt, thresh=opt["thresh"], precision="mixed", split=1e-5).cpu().numpy()
+    err = np.max(np.abs(gmx - g64))
+    print(f"mixed gradient: max|grad_mixed - grad_fp64| = {err:.2e}")
+    assert err <= 1e-5

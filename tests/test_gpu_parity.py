@@ -1,0 +1,141 @@
+"""GPU parity: the CUDA library through the C ABI against the CPU oracle,
+element by element, on seeded synthetic molecules.
+
+Tolerances: FP64 path max|dJ|, max|dK| <= 1e-10 and |dE| <= 1e-9 Eh; mixed
+FP32/FP64 path |dE| <= 1e-6 Eh (its J/K errors are reported and bounded
+loosely).  Quartets whose bound lies within round-off of the threshold may be
+kept by one side and dropped by the other; their contribution is below
+thresh * max|D| per element, far inside the tolerances.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2406_11185_gb300 import adft, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_JK = 1e-10
+TOL_E = 1e-9
+TOL_E_MIXED = 1e-6
+
+
+def _case(name, spherical=True, nocc=None):
+    mol, opt = synth.config(name, spherical=spherical)
+    D = synth.make_density(mol, synth.default_nocc(mol, opt["nocc"] if nocc is None else nocc), opt["dseed"])
+    return mol, opt, D
+
+
+_ref_cache = {}
+
+
+def _oracle_jk(name, spherical, mol, D, thresh):
+    key = (name, spherical, thresh)
+    if key not in _ref_cache:
+        J, K = oracle.jk(mol, D, thresh)
+        _ref_cache[key] = (J, K, oracle.energy(D, J, K))
+    return _ref_cache[key]
+
+
+def _gpu_jk(mol, D, thresh, precision="fp64", split=1e-5):
+    b = adft.Basis.from_molecule(mol)
+    Dt = torch.from_numpy(D).cuda()
+    J, K = adft.adft_jk_build(b, Dt, thresh=thresh, split=split, precision=precision)
+    E = adft.adft_jk_energy(b, Dt, thresh=thresh, split=split, precision=precision)
+    st = adft.adft_jk_last_stats(b)
+    return J.cpu().numpy(), K.cpu().numpy(), E, st, b
+
+
+@pytest.mark.parametrize("name,spherical", [("tiny", True), ("tiny", False), ("small", True), ("tiny_f", True),
+                                            ("tiny_f", False)])
+def test_fp64_parity(name, spherical):
+    mol, opt, D = _case(name, spherical)
+    Jr, Kr, Er = _oracle_jk(name, spherical, mol, D, opt["thresh"])
+    J, K, E, st, _ = _gpu_jk(mol, D, opt["thresh"])
+    dj, dk = np.max(np.abs(J - Jr)), np.max(np.abs(K - Kr))
+    print(f"{name} sph={spherical}: max|dJ|={dj:.2e} max|dK|={dk:.2e} |dE|={abs(E - Er):.2e} stats={st}")
+    assert dj <= TOL_JK and dk <= TOL_JK
+    assert abs(E - Er) <= TOL_E
+    assert st["quartets_fp32"] == 0 and st["quartets_fp64"] > 0
+
+
+@pytest.mark.parametrize("name,split", [("tiny_f", 1e-5), ("small", 1e-5), ("small", 1e-7)])
+def test_mixed_precision_energy(name, split):
+    mol, opt, D = _case(name)
+    Jr, Kr, Er = _oracle_jk(name, True, mol, D, opt["thresh"])
+    J, K, E, st, _ = _gpu_jk(mol, D, opt["thresh"], precision="mixed", split=split)
+    dj, dk = np.max(np.abs(J - Jr)), np.max(np.abs(K - Kr))
+    print(f"{name} split={split}: max|dJ|={dj:.2e} max|dK|={dk:.2e} |dE|={abs(E - Er):.2e} "
+          f"fp64={st['quartets_fp64']} fp32={st['quartets_fp32']}")
+    assert st["quartets_fp32"] > 0
+    assert abs(E - Er) <= TOL_E_MIXED
+    assert dj <= 1e-5 and dk <= 1e-5
+
+
+def test_schwarz_bounds_match_oracle():
+    mol, opt, D = _case("tiny_f")
+    b = adft.Basis.from_molecule(mol)
+    Qg = b.schwarz()
+    Qr = oracle.schwarz(mol)
+    assert np.max(np.abs(Qg - Qr) / np.maximum(Qr, 1e-300)) <= 1e-11
+
+
+def test_screening_threshold_consistency():
+    mol, opt, D = _case("small")
+    Q = oracle.schwarz(mol)
+    thr = float(np.quantile(np.outer(Q, Q), 0.5))
+    Jr, Kr = oracle.jk(mol, D, thr, Q=Q)
+    J, K, E, st, _ = _gpu_jk(mol, D, thr)
+    npair = len(Q)
+    assert 0 < st["quartets_fp64"] < npair * (npair + 1) // 2
+    assert np.max(np.abs(J - Jr)) <= TOL_JK + thr * np.max(np.abs(D)) * 10
+    assert np.max(np.abs(K - Kr)) <= TOL_JK + thr * np.max(np.abs(D)) * 10
+
+
+def test_repeatability_and_symmetry():
+    mol, opt, D = _case("small")
+    b = adft.Basis.from_molecule(mol)
+    Dt = torch.from_numpy(D).cuda()
+    runs = [adft.adft_jk_build(b, Dt, thresh=opt["thresh"]) for _ in range(4)]
+    J0, K0 = (x.cpu().numpy() for x in runs[0])
+    for J, K in runs[1:]:
+        assert np.max(np.abs(J.cpu().numpy() - J0)) <= 1e-13 * np.max(np.abs(J0))
+        assert np.max(np.abs(K.cpu().numpy() - K0)) <= 1e-13 * np.max(np.abs(K0))
+    assert np.max(np.abs(J0 - J0.T)) <= 1e-14 * np.max(np.abs(J0))
+    assert np.max(np.abs(K0 - K0.T)) <= 1e-14 * np.max(np.abs(K0))
+
+
+def test_bad_density_rejected():
+    mol, opt, D = _case("tiny")
+    b = adft.Basis.from_molecule(mol)
+    A = D.copy()
+    A[0, 1] += 1e-3
+    with pytest.raises(adft.AdftError) as e:
+        adft.adft_jk_build(b, torch.from_numpy(A).cuda(), thresh=opt["thresh"])
+    assert e.value.status == adft.ADFT_ERR_ASYM_D
+    A = D.copy()
+    A[2, 2] = np.nan
+    with pytest.raises(adft.AdftError) as e:
+        adft.adft_jk_build(b, torch.from_numpy(A).cuda(), thresh=opt["thresh"])
+    assert e.value.status == adft.ADFT_ERR_NONFINITE
+    with pytest.raises(ValueError):
+        adft.adft_jk_build(b, torch.from_numpy(D[:-1, :-1].copy()).cuda())
+    # the handle still works afterwards
+    J, K = adft.adft_jk_build(b, torch.from_numpy(D).cuda(), thresh=opt["thresh"])
+    Jr, Kr, _ = _oracle_jk("tiny", True, mol, D, opt["thresh"])
+    assert np.max(np.abs(J.cpu().numpy() - Jr)) <= TOL_JK
+
+
+def test_abort_flag_reported():
+    mol, opt, D = _case("tiny")
+    b = adft.Basis.from_molecule(mol)
+    Dt = torch.from_numpy(D).cuda()
+    adft.adft_basis_set_abort(b, True)
+    with pytest.raises(adft.AdftError) as e:
+        adft.adft_jk_build(b, Dt, thresh=opt["thresh"])
+    assert e.value.status == adft.ADFT_ERR_ABORTED
+    adft.adft_basis_set_abort(b, False)
+    J, K = adft.adft_jk_build(b, Dt, thresh=opt["thresh"])
+    assert adft.adft_jk_status(b) == 0
