@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 J/K build (one JSON line on stdout).
+
+A step is one pass of the J/K hot path over one synthetic molecule: the
+screening and work-list pass, the ERI + J/K digestion kernels of both
+precision bands, the spherical transforms and the energy E_JK
+(adft_jk_energy), with the basis (pairs and Schwarz bounds) built once before
+timing, as in an SCF loop.  The metric is screened shell quartets per second
+of the mixed-precision build; the same build in plain FP64 is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl reference]
+
+--impl reference times the CPU oracle (the plain FP64 reference written from
+the paper's definitions) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "J+K build sec & screened quartets/s at ~2k basis fns; mixed vs FP64 at 1e-6 Eh"
+UNIT = "screened quartets/s"
+WORKLOADS = {
+    "c120": "48 heavy (4s3p2d1f) + 72 H (3s2p1d) atoms, 1-8 primitives, exponents 0.05-1e4, "
+            "2448 spherical functions, thresh 1e-12, split 1e-5, mixed FP32/FP64",
+    "c200": "80 heavy (4s3p2d1f) + 120 H (3s2p1d) atoms, 1-8 primitives, exponents 0.05-1e4, "
+            "4080 spherical functions, thresh 1e-12, split 1e-5, mixed FP32/FP64",
+    "c60": "24 heavy (3s2p1d) + 36 H (2s1p) atoms, 1-6 primitives, exponents 0.1-5e3, "
+           "516 spherical functions, thresh 1e-10, split 1e-5, mixed FP32/FP64",
+    "small": "3 heavy (3s2p1d) + 5 H (2s1p) atoms, 1-6 primitives, exponents 0.1-5e3, "
+             "67 spherical functions, thresh 1e-10, split 1e-5, mixed FP32/FP64 (profiling case)",
+}
+# Peaks of plain ALU arithmetic derived from unit counts and the maximum
+# clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz, and the FP64 rate of
+# 2 FMA per SM per clock (1.26 TFLOP/s, the 1.25 TFLOP/s nominal figure).
+SMS, CLK_MAX = 152, 2.07e9
+PEAK_FP32 = SMS * 128 * 2 * CLK_MAX / 1e12
+PEAK_FP64 = SMS * 2 * 2 * CLK_MAX / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(name):
+    from paper_2406_11185_gb300 import synth
+    mol, opt = synth.config(name)
+    nocc = synth.default_nocc(mol, opt["nocc"])
+    D = synth.make_density(mol, nocc, opt["dseed"])
+    return mol, opt, D
+
+
+def cpu_oracle_rate(mol, opt, D, budget_s=15.0, seed=7):
+    """Oracle quartets/s on a bounded sample of the workload: the oracle's
+    whole J/K (Schwarz bounds + screened scatter sum) over a random subset of
+    the molecule's shells (all atoms kept), grown until it takes about
+    budget_s / 4 or more."""
+    import oracle
+    from paper_2406_11185_gb300 import synth
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(mol.nshell)
+    offs = np.cumsum([0] + [2 * l + 1 for _, l, _, _ in mol.shells])
+    k = 12
+    spent = 0.0
+    while True:
+        pick = np.sort(order[:k])
+        sub = synth.Molecule(mol.atoms, mol.heavy, [mol.shells[i] for i in pick], mol.spherical)
+        idx = np.concatenate([np.arange(offs[i], offs[i + 1]) for i in pick])
+        Ds = np.ascontiguousarray(D[np.ix_(idx, idx)])
+        t = time.time()
+        _, _, kept = oracle.jk(sub, Ds, opt["thresh"], return_kept=True)
+        dt = time.time() - t
+        spent += dt
+        if dt > budget_s / 4 or k >= mol.nshell or spent > budget_s:
+            break
+        k = min(mol.nshell, int(k * 1.6) + 1)
+    return {"value": kept / dt if dt > 0 else None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle Schwarz + screened J/K over a random {k} of {mol.nshell} shells "
+                      f"({kept} kept quartets in {dt:.2f} s, all host cores via OpenMP)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    mol, opt, D = workload(args.workload)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(mol, opt, D, budget_s=args.ref_budget)
+        if i >= args.warmup:
+            vals.append(r)
+    v = float(np.median([r["value"] for r in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=os.environ.get("ADFT_BENCH_WORKLOAD", "c60"), choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="adft", choices=["adft", "reference"])
+    ap.add_argument("--ref-budget", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2406_11185_gb300 import adft
+
+    mol, opt, Dn = workload(args.workload)
+    t0 = time.time()
+    basis = adft.Basis.from_molecule(mol)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    D = torch.from_numpy(Dn).to(dev)
+    thresh, split = opt["thresh"], opt["split"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(prec="mixed"):
+        return adft.adft_jk_energy(basis, D, thresh=thresh, split=split, precision=prec, check=False,
+                                   on_device=True)
+
+    # plain FP64 reference build on the same GPU (energy and time)
+    e64 = step("fp64")
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    e64 = step("fp64")
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = ev[0].elapsed_time(ev[1])
+    st64 = adft.adft_jk_last_stats(basis)
+    E64 = float(e64.item())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    times, phases = [], []
+    with ClockSampler(dev.index or 0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e = step()
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            phases.append(adft.adft_jk_last_timings(basis))
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    Emix = float(e.item())
+    st = adft.adft_jk_last_stats(basis)
+    ms_total = float(sum(times))
+    if ws > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    quartets = st["quartets_fp64"] + st["quartets_fp32"]
+    value = ws * quartets / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned D in, J and K out
+    Dh = torch.from_numpy(Dn).pin_memory()
+    Jh = torch.empty_like(Dh).pin_memory()
+    Kh = torch.empty_like(Dh).pin_memory()
+    Jd, Kd, Dd = torch.empty_like(D), torch.empty_like(D), torch.empty_like(D)
+    e2e_ms = []
+    for i in range(2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        Dd.copy_(Dh, non_blocking=True)
+        adft.adft_jk_build(basis, Dd, thresh=thresh, split=split, precision="mixed", check=True, out=(Jd, Kd))
+        Jh.copy_(Jd, non_blocking=True)
+        Kh.copy_(Kd, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i > 0:
+            e2e_ms.append(a.elapsed_time(b))
+    nb2 = Dn.size * 8
+
+    # roofline of the dominant kernel group (ALU-bound ERI kernels)
+    ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
+    groups = {"eri_fp32": (ph["eri_fp32_ms"], st["flops_fp32"], PEAK_FP32),
+              "eri_fp64": (ph["eri_fp64_ms"], st["flops_fp64"], PEAK_FP64)}
+    dom = max(groups, key=lambda k: groups[k][0])
+    gms, gfl, gpk = groups[dom]
+    ach = gfl / (gms / 1e3) / 1e12 if gms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": f"{dom} (all class-pair launches of the band)", "achieved": ach,
+            "peak": gpk, "unit": "TFLOP/s", "frac": ach / gpk, "traffic": None,
+            "peak_kind": "derived: 152 SMs x lanes x 2 x 2.07 GHz",
+            "other": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0,
+                          "frac": ((v[1] / (v[0] / 1e3) / 1e12) / v[2]) if v[0] > 0 else 0.0}
+                      for k, v in groups.items()}}
+    line ={"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "nbf": basis.nbf,
+                       "natom": mol.natom, "nshell": mol.nshell, "thresh": thresh, "split": split,
+                       "precision": "mixed", "l2": "flushed before every step (256 MB write)",
+                       "parallelism": f"replicas x{ws}"},
+            "jk_build_s_mixed": ms / 1e3, "jk_build_s_fp64": fp64_ms / 1e3,
+            "speedup_mixed_vs_fp64": fp64_ms / ms, "energy_mixed": Emix, "energy_fp64": E64,
+            "energy_err_mixed_vs_fp64": abs(Emix - E64),
+            "quartets": {"fp64": st["quartets_fp64"], "fp32": st["quartets_fp32"],
+                         "unique_before_screening": st["quartets_total"],
+                         "prim_fp64": st["prim_quartets_fp64"], "prim_fp32": st["prim_quartets_fp32"],
+                         "fp64_only_build": st64["quartets_fp64"]},
+            "phases_ms": ph, "setup_s": setup_s,
+            "clocks": clk.summary(),
+            "e2e": {"value": ws * quartets / (np.mean(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
+                    "d2h_bytes_per_step": 2 * nb2, "ms": float(np.mean(e2e_ms))},
+            "gpu_launches": None, "roofline": roof}
+    line["gpu_launches"] = launches_per_step(basis_classes(mol), mixed=True) * args.steps
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_rate(mol, opt, Dn)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def basis_classes(mol):
+    """Number of non-empty pair classes (l_a >= l_b) of the molecule."""
+    ls = sorted({l for _, l, _, _ in mol.shells})
+    present = set()
+    for a in ls:
+        for b in ls:
+            if a >= b:
+                present.add((a, b))
+    return len(present)
+
+
+def launches_per_step(ncls, mixed=True):
+    """Kernels of one adft_jk_energy call: D transform, screen, scan, one ERI
+    kernel per class pair and band, output transform, energy."""
+    ncp = ncls * (ncls + 1) // 2
+    return 5 + ncp * (2 if mixed else 1)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

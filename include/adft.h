@@ -154,6 +154,34 @@ int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* opts, double* 
  * this handle (synchronises the handle's last stream). */
 int adft_jk_last_stats(adft_basis* b, adft_stats* st);
 
+/* Device time of the phases of the last adft_jk_build / adft_jk_energy /
+ * adft_jk_grad on this handle, from CUDA events recorded on its stream
+ * (synchronises on the last event).  ms: host [4] milliseconds:
+ *   [0] D check, D -> Cartesian, screening and work-list scan,
+ *   [1] the FP64 ERI (or derivative) kernels, [2] the FP32 ones (0 unless
+ *   mixed), [3] Cartesian -> output transform and energy. */
+int adft_jk_last_timings(adft_basis* b, double* ms);
+
+/* Autotuner (per angular-momentum class pair and precision band): times
+ * every class-pair kernel of one build of D with 1, 2, 4, 8 and 16 resident
+ * blocks per SM and keeps the fastest launch shape in the handle for later
+ * calls.  The J/K accumulators of the handle are left undefined.
+ *   table: host [2][55] ints (band-major: FP64 then FP32; class pair
+ *   X(X+1)/2 + Y with class X = l_a(l_a+1)/2 + l_b) or NULL.
+ *   ms: host [2][55] doubles, the best time of every class-pair kernel
+ *   (0 for empty ones), or NULL.
+ * Synchronous. */
+int adft_autotune(adft_basis* b, const double* D, const adft_opts* opts, int* table, double* ms);
+
+/* Plan only: run the screening and work-list pass for D (no integrals) and
+ * report what a build would evaluate.  st: the counts of adft_jk_last_stats
+ * (flops are the counted estimate); quartets: host [2][55] int64 shell
+ * quartets per band and class pair, or NULL.  Synchronous. */
+int adft_jk_plan(adft_basis* b, const double* D, const adft_opts* opts, adft_stats* st, int64_t* quartets);
+
+/* Install a launch-shape table (same layout as adft_autotune's). */
+int adft_set_tuning(adft_basis* b, const int* table);
+
 /* Raise (1) or clear (0) the handle's abort flag.  A running or later build
  * sees it on the device and returns ADFT_ERR_ABORTED (with opts->check = 1)
  * or leaves a status readable by adft_jk_status. */
@@ -179,13 +207,27 @@ int adft_batch_offsets(const adft_batch* bt, int64_t* offsets);
 int adft_batch_grad_offsets(const adft_batch* bt, int64_t* offsets);
 
 /* J, K (and optionally E and the gradient) of every molecule with one
- * persistent launch per angular-momentum class over a global quartet work
- * list spanning all molecules.
+ * persistent launch per angular-momentum class pair and band over a global
+ * quartet work list spanning all molecules (the batch is built as one basis
+ * whose shell pairs never mix molecules).
  *   D_packed, J_packed, K_packed: dev, packed per adft_batch_offsets.
  *   E: dev [nmol] or NULL.  grad_packed: dev per adft_batch_grad_offsets or
- *   NULL. */
+ *   NULL.
+ * With opts->check = 0 and a non-NULL stream the whole call is captured into
+ * a CUDA graph on first use and replayed by later calls with the same
+ * buffers and options; the first call must not itself run inside a stream
+ * capture.  With opts->check = 1 the launches are issued directly and the
+ * stream is synchronised to report the validation result. */
 int adft_batch_jk(adft_batch* bt, const double* D_packed, const adft_opts* opts, double* J_packed,
                   double* K_packed, double* E, double* grad_packed);
+
+/* Statistics and phase times of the last adft_batch_jk (see
+ * adft_jk_last_stats / adft_jk_last_timings). */
+int adft_batch_last_stats(adft_batch* bt, adft_stats* st);
+int adft_batch_last_timings(adft_batch* bt, double* ms);
+
+/* The autotuner of the batch's class-pair kernels (see adft_autotune). */
+int adft_batch_autotune(adft_batch* bt, const double* D_packed, const adft_opts* opts, int* table, double* ms);
 
 void adft_batch_destroy(adft_batch* bt);
 

@@ -52,6 +52,8 @@ def lib():
         L.orc_schwarz.argtypes = basis + [dp, ctypes.c_int]
         L.orc_jk.argtypes = basis + [dp, ctypes.c_double, dp, dp, dp, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_long)]
+        L.orc_jk_range.argtypes = basis + [dp, ctypes.c_double, dp, dp, dp, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_long), ctypes.c_long, ctypes.c_long]
         L.orc_jk_blocks.argtypes = basis + [dp, ctypes.c_double, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int]
         L.orc_eri_tensor.argtypes = basis + [dp]
         L.orc_overlap.argtypes = basis + [dp]
@@ -253,6 +255,22 @@ def jk(mol, D, thresh, Q=None, nthreads=None, return_kept=False):
                  _nthreads(nthreads), ctypes.byref(kept))
     J, K = _from_cart(mol, J), _from_cart(mol, K)
     return (J, K, kept.value) if return_kept else (J, K)
+
+
+def jk_range_count(mol, D, thresh, ab_lo, ab_hi, Q=None, nthreads=None) -> int:
+    """Run the scatter-mode J/K sum over bra pairs [ab_lo, ab_hi) only (pair
+    index a(a+1)/2+b in creation order) and return the number of kept shell
+    quartets; used to time a bounded sample of the oracle."""
+    B = _Basis(mol)
+    if Q is None:
+        Q = schwarz(mol, nthreads)
+    Dc = _to_cart(mol, np.asarray(D, dtype=np.float64))
+    J = np.zeros((B.nc, B.nc))
+    K = np.zeros((B.nc, B.nc))
+    kept = ctypes.c_long(0)
+    lib().orc_jk_range(*B.args(), _p(np.ascontiguousarray(Q)), float(thresh), _p(Dc), _p(J), _p(K),
+                       _nthreads(nthreads), ctypes.byref(kept), int(ab_lo), int(ab_hi))
+    return kept.value
 
 
 def energy(D, J, K) -> float:

@@ -377,14 +377,32 @@ static void scatter_jk(const int *sh, const int *off, const int *nsz, const doub
   }
 }
 
+static void jk_range(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
+                     const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
+                     const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi);
+
 void orc_jk(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
             const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
             const double *D, double *J, double *K, int nthreads, long *nkept) {
+  jk_range(xyz, nshell, atom, l, nprim, ptr, exps, coefs, Q, thresh, D, J, K, nthreads, nkept, 0,
+           (long)nshell * (nshell + 1) / 2);
+}
+
+/* The same sum restricted to bra pairs ab in [ab_lo, ab_hi) (each with all
+   its kets cd <= ab): a bounded sample of the work for timing. */
+void orc_jk_range(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
+                  const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
+                  const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi) {
+  jk_range(xyz, nshell, atom, l, nprim, ptr, exps, coefs, Q, thresh, D, J, K, nthreads, nkept, ab_lo, ab_hi);
+}
+
+static void jk_range(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
+                     const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
+                     const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi) {
   orc_basis bs = {xyz, nshell, atom, l, nprim, ptr, exps, coefs};
   int *off = (int *)malloc(sizeof(int) * (nshell + 1));
   shell_offsets(&bs, off);
   const int nc = off[nshell];
-  const long npair = (long)nshell * (nshell + 1) / 2;
   memset(J, 0, sizeof(double) * nc * nc);
   memset(K, 0, sizeof(double) * nc * nc);
   long kept = 0;
@@ -397,7 +415,7 @@ void orc_jk(const double *xyz, int nshell, const int *atom, const int *l, const 
     double *Kt = (double *)calloc((size_t)nc * nc, sizeof(double));
     double *blk = (double *)malloc(sizeof(double) * 15 * 15 * 15 * 15);
 #pragma omp for schedule(dynamic, 1)
-    for (long ab = npair - 1; ab >= 0; --ab) {
+    for (long ab = ab_hi - 1; ab >= ab_lo; --ab) {
       int a = 0;
       while ((long)(a + 1) * (a + 2) / 2 <= ab) ++a;
       const int b = (int)(ab - (long)a * (a + 1) / 2);

@@ -30,9 +30,10 @@ ADFT_MAX_NPRIM = 16
 
 EXPORTED = [
     "adft_basis_create", "adft_basis_nbf", "adft_basis_dims", "adft_basis_schwarz", "adft_jk_build",
-    "adft_jk_energy", "adft_jk_grad", "adft_jk_last_stats", "adft_basis_set_abort", "adft_jk_status",
+    "adft_jk_energy", "adft_jk_grad", "adft_jk_last_stats", "adft_jk_last_timings", "adft_basis_set_abort", "adft_jk_status",
     "adft_basis_destroy", "adft_batch_create", "adft_batch_offsets", "adft_batch_grad_offsets", "adft_batch_jk",
-    "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version",
+    "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version", "adft_autotune",
+    "adft_set_tuning", "adft_jk_plan", "adft_batch_last_stats", "adft_batch_last_timings", "adft_batch_autotune",
 ]
 
 
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH):
     L.adft_jk_energy.argtypes = [vp, vp, ctypes.POINTER(adft_opts), vp, ip]
     L.adft_jk_grad.argtypes = [vp, vp, ctypes.POINTER(adft_opts), vp]
     L.adft_jk_last_stats.argtypes = [vp, ctypes.POINTER(adft_stats)]
+    L.adft_jk_last_timings.argtypes = [vp, dp]
     L.adft_basis_set_abort.argtypes = [vp, ip]
     L.adft_jk_status.argtypes = [vp]
     L.adft_basis_destroy.argtypes = [vp]
@@ -89,6 +91,13 @@ def load(path: str = LIB_PATH):
     L.adft_batch_jk.argtypes = [vp, vp, ctypes.POINTER(adft_opts), vp, vp, vp, vp]
     L.adft_batch_destroy.argtypes = [vp]
     L.adft_batch_destroy.restype = None
+    L.adft_autotune.argtypes = [vp, vp, ctypes.POINTER(adft_opts), ctypes.POINTER(ctypes.c_int), dp]
+    L.adft_set_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.adft_jk_plan.argtypes = [vp, vp, ctypes.POINTER(adft_opts), ctypes.POINTER(adft_stats),
+                               ctypes.POINTER(ctypes.c_int64)]
+    L.adft_batch_last_stats.argtypes = [vp, ctypes.POINTER(adft_stats)]
+    L.adft_batch_last_timings.argtypes = [vp, dp]
+    L.adft_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(adft_opts), ctypes.POINTER(ctypes.c_int), dp]
     L.adft_status_string.argtypes = [ip]
     L.adft_status_string.restype = ctypes.c_char_p
     L.adft_last_error_message.restype = ctypes.c_char_p
@@ -225,9 +234,134 @@ def adft_jk_last_stats(basis: Basis) -> dict:
     return {k: getattr(st, k) for k, _ in adft_stats._fields_}
 
 
+def adft_jk_last_timings(basis: Basis) -> dict:
+    """Device milliseconds of the phases of the last call (CUDA events)."""
+    ms = (ctypes.c_double * 4)()
+    _check(load().adft_jk_last_timings(basis.handle, ms), "adft_jk_last_timings")
+    return {"setup_screen_ms": ms[0], "eri_fp64_ms": ms[1], "eri_fp32_ms": ms[2], "transform_ms": ms[3]}
+
+
 def adft_basis_set_abort(basis: Basis, flag: bool):
     _check(load().adft_basis_set_abort(basis.handle, 1 if flag else 0), "adft_basis_set_abort")
 
 
 def adft_jk_status(basis: Basis) -> int:
     return int(load().adft_jk_status(basis.handle))
+
+
+NCP = 55  # class pairs up to f shells
+
+
+def adft_autotune(basis: Basis, D, thresh=1e-12, split=1e-5, precision="mixed", stream=None,
+                  return_times=False):
+    """Run the launch-shape autotuner on density D; returns the [2, 55] table
+    of blocks per SM (FP64 band, FP32 band) now installed in the handle (and
+    the best kernel time of every class pair in ms with return_times)."""
+    _check_matrix(D, basis.nbf)
+    tab = (ctypes.c_int * (2 * NCP))()
+    ms = (ctypes.c_double * (2 * NCP))()
+    o = make_opts(thresh, split, precision, False, stream)
+    _check(load().adft_autotune(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o), tab, ms),
+           "adft_autotune")
+    t = np.array(tab[:], dtype=np.int32).reshape(2, NCP)
+    return (t, np.array(ms[:]).reshape(2, NCP)) if return_times else t
+
+
+def adft_jk_plan(basis: Basis, D, thresh=1e-12, split=1e-5, precision="mixed", stream=None):
+    """Screening only: (stats dict, [2, 55] shell quartets per band and class pair)."""
+    _check_matrix(D, basis.nbf)
+    st = adft_stats()
+    q = (ctypes.c_int64 * (2 * NCP))()
+    o = make_opts(thresh, split, precision, False, stream)
+    _check(load().adft_jk_plan(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o), ctypes.byref(st), q),
+           "adft_jk_plan")
+    return {k: getattr(st, k) for k, _ in adft_stats._fields_}, np.array(q[:], dtype=np.int64).reshape(2, NCP)
+
+
+def adft_set_tuning(basis: Basis, table) -> None:
+    t = np.ascontiguousarray(np.asarray(table, dtype=np.int32).reshape(-1))
+    if t.size != 2 * NCP:
+        raise ValueError("table must hold 2 x 55 entries")
+    _check(load().adft_set_tuning(basis.handle, t.ctypes.data_as(ctypes.POINTER(ctypes.c_int))), "adft_set_tuning")
+
+
+class Batch:
+    """Owns an adft_batch of several bases (adft_batch_create / destroy)."""
+
+    def __init__(self, bases):
+        L = load()
+        self.bases = list(bases)
+        arr = (ctypes.c_void_p * len(self.bases))(*[b.handle.value for b in self.bases])
+        h = ctypes.c_void_p()
+        _check(L.adft_batch_create(arr, len(self.bases), ctypes.byref(h)), "adft_batch_create")
+        self.handle = h
+        self.nmol = len(self.bases)
+        off = (ctypes.c_int64 * (self.nmol + 1))()
+        _check(L.adft_batch_offsets(h, off), "adft_batch_offsets")
+        self.offsets = np.array(off[:], dtype=np.int64)
+        goff = (ctypes.c_int64 * (self.nmol + 1))()
+        _check(L.adft_batch_grad_offsets(h, goff), "adft_batch_grad_offsets")
+        self.grad_offsets = np.array(goff[:], dtype=np.int64)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            load().adft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, mats):
+        import torch
+        return torch.cat([m.reshape(-1) for m in mats]).contiguous()
+
+    def unpack(self, flat):
+        out = []
+        for i, b in enumerate(self.bases):
+            out.append(flat[self.offsets[i]:self.offsets[i + 1]].reshape(b.nbf, b.nbf))
+        return out
+
+
+def adft_batch_jk(batch: Batch, D_packed, thresh=1e-10, split=1e-5, precision="mixed", check=False, stream=None,
+                  energy=True, grad=False, out=None):
+    """Packed J, K (and per-molecule E, packed gradient) of every molecule."""
+    import torch
+    if not (isinstance(D_packed, torch.Tensor) and D_packed.is_cuda and D_packed.dtype == torch.float64
+            and D_packed.is_contiguous() and D_packed.numel() == int(batch.offsets[-1])):
+        raise ValueError("D_packed must be a contiguous CUDA float64 tensor of the packed size")
+    if out is None:
+        J, K = torch.empty_like(D_packed), torch.empty_like(D_packed)
+        E = torch.empty(batch.nmol, dtype=torch.float64, device=D_packed.device) if energy else None
+        G = torch.empty(int(batch.grad_offsets[-1]), dtype=torch.float64, device=D_packed.device) if grad else None
+    else:
+        J, K, E, G = out
+    o = make_opts(thresh, split, precision, check, stream)
+    vp = ctypes.c_void_p
+    _check(load().adft_batch_jk(batch.handle, vp(D_packed.data_ptr()), ctypes.byref(o), vp(J.data_ptr()),
+                                vp(K.data_ptr()), vp(E.data_ptr()) if E is not None else None,
+                                vp(G.data_ptr()) if G is not None else None), "adft_batch_jk")
+    return J, K, E, G
+
+
+def adft_batch_last_stats(batch: Batch) -> dict:
+    st = adft_stats()
+    _check(load().adft_batch_last_stats(batch.handle, ctypes.byref(st)), "adft_batch_last_stats")
+    return {k: getattr(st, k) for k, _ in adft_stats._fields_}
+
+
+def adft_batch_last_timings(batch: Batch) -> dict:
+    ms = (ctypes.c_double * 4)()
+    _check(load().adft_batch_last_timings(batch.handle, ms), "adft_batch_last_timings")
+    return {"setup_screen_ms": ms[0], "eri_fp64_ms": ms[1], "eri_fp32_ms": ms[2], "transform_ms": ms[3]}
+
+
+def adft_batch_autotune(batch: Batch, D_packed, thresh=1e-10, split=1e-5, precision="mixed",
+                        stream=None) -> np.ndarray:
+    tab = (ctypes.c_int * (2 * NCP))()
+    o = make_opts(thresh, split, precision, False, stream)
+    _check(load().adft_batch_autotune(batch.handle, ctypes.c_void_p(D_packed.data_ptr()), ctypes.byref(o), tab,
+                                      None), "adft_batch_autotune")
+    return np.array(tab[:], dtype=np.int32).reshape(2, NCP)

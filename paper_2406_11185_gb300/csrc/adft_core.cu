@@ -1,5 +1,12 @@
 // Host orchestration and the data-parallel setup / screening / transform
 // kernels of the GB300 J/K library.  Public entry points: include/adft.h.
+//
+// A basis holds one molecule; a batch is a basis holding several molecules:
+// shells and atoms are concatenated, shell pairs are formed only inside a
+// molecule and grouped by angular-momentum class, then by molecule, then by
+// descending Schwarz bound.  Every per-call array (Cartesian D, J, K) is
+// packed molecule after molecule, so one persistent kernel per class pair
+// serves all molecules of a batch.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -7,9 +14,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "adft_internal.cuh"
@@ -128,19 +137,22 @@ static void sph_coefficients(double out[LMAX + 1][2 * LMAX + 1][SPH_MAXC]) {
 // basis handle
 
 struct Workspace {
-  double* Dc = nullptr;     // Cartesian D
+  double* Dc = nullptr;     // Cartesian D, packed per molecule
   float* Dc32 = nullptr;
-  double* Jc = nullptr;     // Cartesian accumulators
+  double* Jc = nullptr;     // Cartesian accumulators (unsymmetrised)
   double* Kc = nullptr;
-  double* Jw = nullptr;     // J, K in the output basis (energy / gradient calls)
+  double* Jw = nullptr;     // J, K in the output basis (energy calls)
   double* Kw = nullptr;
-  int* cnt64 = nullptr;     // per (class pair, bra) kept FP64 kets
-  int* cnt32 = nullptr;     // per (class pair, bra) kept FP32 kets
-  long long* pre64 = nullptr;  // per (class pair) prefix arrays
+  int* cnt64 = nullptr;     // per (class pair, bra): kept FP64 kets
+  int* cnt32 = nullptr;     //                        kept FP32 kets
+  int* kst64 = nullptr;     //                        first FP64 ket - class start
+  int* kst32 = nullptr;     //                        first FP32 ket - class start
+  long long* pre64 = nullptr;  // per class pair: prefix sums over its bras
   long long* pre32 = nullptr;
-  unsigned long long* counters = nullptr;  // [2 * NCP]
-  int* status = nullptr;    // [4]: status, abort flag
+  unsigned long long* counters = nullptr;  // [2 passes][2 * NCP] work counters
+  int* status = nullptr;    // [4]: status word, abort flag
   double* scal = nullptr;   // [4]: energy, max|D|, max|D-D^T|
+  double* Emol = nullptr;   // [nmol] energies
   unsigned long long* stats = nullptr;     // [8]
 };
 
@@ -148,38 +160,59 @@ struct Workspace {
 
 struct adft_basis {
   int device = 0;
-  int natom = 0, nshell = 0, ncart = 0, nbf = 0, spherical = 1;
-  std::vector<int> shell_l, shell_atom, shell_nprim, shell_poff, shell_coff, shell_soff;
+  int nmol = 1;
+  int natom = 0, nshell = 0, ncart = 0, nbf = 0, spherical = 1;  // totals
+  std::vector<int> mol_atom_off, mol_shell_off, mol_cf_off, mol_f_off;  // [nmol+1]
+  std::vector<int> mol_nc, mol_nbf;                                     // [nmol]
+  std::vector<long long> mol_cbase, mol_obase;                          // [nmol+1] packed n^2 offsets
+  std::vector<int> shell_l, shell_atom, shell_nprim, shell_poff, shell_coff, shell_soff, shell_mol;
   std::vector<double> xyz, exps, ncoefs;  // ncoefs: c_i N(a_i, l)
-  // pairs in class order (sorted by Q descending inside each class)
+  // pairs: class-major, then molecule, then descending Q
   int npair = 0;
   int cls_first[adft::NCLS + 1];
+  std::vector<int> seg_first;  // [NCLS][nmol+1]: first pair of class X of molecule m
   std::vector<int> pair_a, pair_b;
   std::vector<double> pair_Q;
-  long long npp = 0;
-  // per class pair: offset of its per-bra count arrays and its prefix array
+  long long npp = 0, npp_dense = 0;
   long long cnt_off[adft::NCP];
   long long pre_off[adft::NCP];
-  long long cnt_total = 0, pre_total = 0;
   // device arrays
   int *d_shell_l = nullptr, *d_shell_atom = nullptr, *d_shell_coff = nullptr, *d_shell_soff = nullptr;
   int *d_shell_nprim = nullptr, *d_shell_poff = nullptr;
   double *d_xyz = nullptr, *d_exps = nullptr, *d_ncoefs = nullptr;
-  int *d_pair_a = nullptr, *d_pair_b = nullptr, *d_pair_ppoff = nullptr, *d_pair_ppn = nullptr;
+  int *d_pair_a = nullptr, *d_pair_b = nullptr, *d_pair_ppoff = nullptr, *d_pair_ppn = nullptr, *d_pair_mol = nullptr;
   double *d_pair_Q = nullptr, *d_pair_AB = nullptr;
   long long* d_cumppn = nullptr;
+  int* d_seg_first = nullptr;
+  int *d_mol_nc = nullptr, *d_mol_nbf = nullptr, *d_mol_cf_off = nullptr, *d_mol_f_off = nullptr;
+  long long *d_mol_cbase = nullptr, *d_mol_obase = nullptr;
   adft::PrimPair<double>* d_pp64 = nullptr;
   adft::PrimPair<float>* d_pp32 = nullptr;
+  int* d_pp_src = nullptr;    // [npp] (ia << 8) | ib
   double* d_ppw64 = nullptr;  // [2][npp] 2a, 2b
+  double* d_o2p64 = nullptr;  // [npp] 1/(2p)
+  float* d_o2p32 = nullptr;
   float* d_ppw32 = nullptr;
-  int *d_func_shell = nullptr, *d_func_comp = nullptr;  // output-basis function -> (shell, component)
+  int *d_func_shell = nullptr, *d_func_comp = nullptr;    // output function -> (shell, component)
   int *d_cfunc_shell = nullptr, *d_cfunc_comp = nullptr;  // Cartesian function -> (shell, component)
   const double* boys64 = nullptr;
   const float* boys32 = nullptr;
   adft::Workspace ws;
   cudaStream_t last_stream = nullptr;
-  int last_prec = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int ev_valid = 0;
+  int tune_blocks[2][adft::NCP];  // blocks per SM of every class-pair kernel and band (autotuner)
+  int sms = 152;
   std::vector<void*> allocations;
+};
+
+struct adft_batch {
+  adft_basis* b = nullptr;  // the concatenated basis (owned)
+  // CUDA graph of the last captured call
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  std::tuple<const void*, const void*, const void*, const void*, const void*, double, double, int, void*> key;
+  bool has_graph = false;
 };
 
 namespace adft {
@@ -213,17 +246,21 @@ static BasisView view(const adft_basis* b) {
   v.pair_pp_off = b->d_pair_ppoff; v.pair_pp_n = b->d_pair_ppn; v.pair_AB = b->d_pair_AB;
   v.pp64 = b->d_pp64; v.pp32 = b->d_pp32; v.boys64 = b->boys64; v.boys32 = b->boys32;
   v.pp_w64 = b->d_ppw64; v.pp_w32 = b->d_ppw32; v.npp = b->npp;
+  v.pp_o2p64 = b->d_o2p64; v.pp_o2p32 = b->d_o2p32;
+  v.pair_mol = (b->nmol > 1) ? b->d_pair_mol : nullptr;
+  v.mol_cbase = b->d_mol_cbase; v.mol_nc = b->d_mol_nc;
   return v;
 }
 
 // ---------------------------------------------------------------------------
 // a1: primitive-pair construction, one thread per primitive pair.
 __global__ void k_build_pairs(int npair, const int* __restrict__ pair_a, const int* __restrict__ pair_b,
-                              const int* __restrict__ ppoff, const int* __restrict__ shell_atom,
-                              const int* __restrict__ shell_nprim, const int* __restrict__ shell_poff,
+                              const int* __restrict__ ppoff, const int* __restrict__ pp_src,
+                              const int* __restrict__ shell_atom, const int* __restrict__ shell_poff,
                               const double* __restrict__ xyz, const double* __restrict__ exps,
                               const double* __restrict__ ncoefs, long long npp, PrimPair<double>* pp64,
-                              PrimPair<float>* pp32, double* pairAB, double* w64, float* w32) {
+                              PrimPair<float>* pp32, double* w64, float* w32, double* o2p64, float* o2p32,
+                              int* pp_pair) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= npp) return;
   // pair owning primitive pair g (ppoff is ascending)
@@ -233,9 +270,7 @@ __global__ void k_build_pairs(int npair, const int* __restrict__ pair_a, const i
     if (ppoff[mid] <= g) lo = mid; else hi = mid;
   }
   const int pr = lo, sa = pair_a[pr], sb = pair_b[pr];
-  const int local = (int)(g - ppoff[pr]);
-  const int nb = shell_nprim[sb];
-  const int ia = local / nb, ib = local % nb;
+  const int ia = pp_src[g] >> 8, ib = pp_src[g] & 255;  // primitive indices in shells a and b
   const double a = exps[shell_poff[sa] + ia], b = exps[shell_poff[sb] + ib];
   const double* A = xyz + 3 * shell_atom[sa];
   const double* B = xyz + 3 * shell_atom[sb];
@@ -244,25 +279,27 @@ __global__ void k_build_pairs(int npair, const int* __restrict__ pair_a, const i
   const double Px = (a * A[0] + b * B[0]) / p, Py = (a * A[1] + b * B[1]) / p, Pz = (a * A[2] + b * B[2]) / p;
   const double K = ncoefs[shell_poff[sa] + ia] * ncoefs[shell_poff[sb] + ib] *
                    exp(-mu * (ABx * ABx + ABy * ABy + ABz * ABz));
-  PrimPair<double> r{Px, Py, Pz, p, Px - A[0], Py - A[1], Pz - A[2], K};
-  pp64[g] = r;
-  PrimPair<float> f{(float)Px, (float)Py, (float)Pz, (float)p, (float)(Px - A[0]), (float)(Py - A[1]),
-                    (float)(Pz - A[2]), (float)K};
-  pp32[g] = f;
+  pp64[g] = PrimPair<double>{Px, Py, Pz, p, Px - A[0], Py - A[1], Pz - A[2], K};
+  pp32[g] = PrimPair<float>{(float)Px, (float)Py, (float)Pz, (float)p, (float)(Px - A[0]), (float)(Py - A[1]),
+                            (float)(Pz - A[2]), (float)K};
   w64[g] = 2.0 * a; w64[npp + g] = 2.0 * b;
+  o2p64[g] = 0.5 / p;
+  o2p32[g] = (float)(0.5 / p);
   w32[g] = (float)(2.0 * a); w32[npp + g] = (float)(2.0 * b);
-  if (local == 0) {
-    pairAB[3 * pr] = ABx; pairAB[3 * pr + 1] = ABy; pairAB[3 * pr + 2] = ABz;
-  }
+  if (pp_pair) pp_pair[g] = pr;
 }
 
 // ---------------------------------------------------------------------------
-// a3: screening.  For every bra pair i (class X) and ket class Y <= X, the
-// kept kets are a prefix of Y's list (sorted by Q descending): count those
-// with Q_i Q_k >= thresh and, of them, those with Q_i Q_k >= split (FP64).
+// a3: screening.  For every bra pair i (class X, molecule m) and ket class
+// Y <= X, the kept kets are a prefix of molecule m's segment of class Y
+// (sorted by descending Q): those with Q_i Q_k >= thresh; of them the FP64
+// ones are those with Q_i Q_k >= split.
 struct ScreenArgs {
   int cls_first[NCLS + 1];
   long long cnt_off[NCP];
+  int nmol;
+  const int* seg_first;     // [NCLS][nmol+1]
+  const int* pair_mol;      // [npair] or NULL (one molecule)
   const double* Q;
   const int* ppn;
   const long long* cumppn;  // [npair + 1] running sum of ppn in pair order
@@ -270,12 +307,15 @@ struct ScreenArgs {
   int mixed;
   int* cnt64;
   int* cnt32;
-  unsigned long long* stats;  // [0] q64 [1] q32 [2] total unique [3] prim64 [4] prim32
+  int* kst64;
+  int* kst32;
+  unsigned long long* stats;  // [0] q64 [1] q32 [2] total unique [3] prim64 [4] prim32 [5] flop64 [6] flop32
+  float f_pq[NCP], f_bra[NCP], f_q[NCP];
 };
 
 __device__ __forceinline__ int count_prefix(const double* Q, int first, int n, double Qi, double thr) {
   // number of leading k in [first, first+n) with Qi * Q[k] >= thr
-  int lo = 0, hi = n;  // answer in [lo, hi]
+  int lo = 0, hi = n;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (Qi * Q[first + mid] >= thr) lo = mid + 1; else hi = mid;
@@ -286,26 +326,34 @@ __device__ __forceinline__ int count_prefix(const double* Q, int first, int n, d
 __global__ void k_screen(ScreenArgs a, int npair) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long q64 = 0, q32 = 0, tot = 0, p64 = 0, p32 = 0;
+  double f64 = 0.0, f32 = 0.0;
   if (i < npair) {
     int X = 0;
     while (a.cls_first[X + 1] <= i) ++X;
-    const int li = i - a.cls_first[X];
+    const int m = a.pair_mol ? a.pair_mol[i] : 0;
+    const int W = a.nmol + 1;
+    const int li = i - a.seg_first[X * W + m];  // index inside the molecule's class segment
     const double Qi = a.Q[i];
     const int nppi = a.ppn[i];
     for (int Y = 0; Y <= X; ++Y) {
-      const int f = a.cls_first[Y];
-      int n = a.cls_first[Y + 1] - f;
+      const int f = a.seg_first[Y * W + m];
+      int n = a.seg_first[Y * W + m + 1] - f;
       if (Y == X) n = li + 1;
       const int keep = count_prefix(a.Q, f, n, Qi, a.thresh);
       int n64 = keep;
       if (a.mixed) n64 = min(keep, count_prefix(a.Q, f, n, Qi, a.split));
-      const long long o = a.cnt_off[cp_index(X, Y)] + li;
+      const int cp = cp_index(X, Y);
+      const long long o = a.cnt_off[cp] + (i - a.cls_first[X]);
       a.cnt64[o] = n64;
       a.cnt32[o] = keep - n64;
+      a.kst64[o] = f - a.cls_first[Y];
+      a.kst32[o] = f - a.cls_first[Y] + n64;
       q64 += n64; q32 += keep - n64; tot += n;
       const unsigned long long s64 = a.cumppn[f + n64] - a.cumppn[f];
       const unsigned long long s32 = a.cumppn[f + keep] - a.cumppn[f + n64];
       p64 += s64 * nppi; p32 += s32 * nppi;
+      f64 += (double)a.f_pq[cp] * nppi * s64 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * n64;
+      f32 += (double)a.f_pq[cp] * nppi * s32 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * (keep - n64);
     }
   }
   // warp-reduce the statistics, one atomic per warp
@@ -315,11 +363,69 @@ __global__ void k_screen(ScreenArgs a, int npair) {
     tot += __shfl_down_sync(0xffffffffu, tot, o);
     p64 += __shfl_down_sync(0xffffffffu, p64, o);
     p32 += __shfl_down_sync(0xffffffffu, p32, o);
+    f64 += __shfl_down_sync(0xffffffffu, f64, o);
+    f32 += __shfl_down_sync(0xffffffffu, f32, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(a.stats + 0, q64); atomicAdd(a.stats + 1, q32); atomicAdd(a.stats + 2, tot);
     atomicAdd(a.stats + 3, p64); atomicAdd(a.stats + 4, p32);
+    atomicAdd(a.stats + 5, (unsigned long long)f64); atomicAdd(a.stats + 6, (unsigned long long)f32);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Counted arithmetic of the ERI kernels (FMA = 2 flops; exp, sqrt and
+// divisions count 1), per primitive quartet, per bra primitive and per
+// contracted quartet of a class, following the loop structure of
+// quartet_block / digest.  Used for the reported FLOP/s only.
+struct ClassFlops { double per_pq, per_bra, per_q; };
+
+static int herm_count(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+
+static ClassFlops class_flops(int la, int lb, int lc, int ld) {
+  const int NB = ncart(lb), ND = ncart(ld);
+  const int NAB = ncart(la) * NB, NCD = ncart(lc) * ND;
+  const int L = la + lb + lc + ld, NHAB = herm_count(la + lb);
+  const bool small = (L <= 4 && NAB * NCD <= 81);
+  int ck = NCD, nchunk = 1;
+  if (!small) {
+    const int raw = 640 / (NAB + NHAB);
+    ck = raw < 1 ? 1 : (raw > NCD ? NCD : raw);
+    nchunk = (NCD + ck - 1) / ck;
+  }
+  double boys = 12 + 1 + 3.0 * L + 4;
+  double rrec = 0;
+  for (int k = 0; k <= L; ++k) rrec += 3.0 * herm_count(k);
+  const double ecd = 3 * 3.0 * (lc + 1) * (ld + 1) * (lc + ld + 1);
+  double ket = 0;
+  for (int kc = 0; kc < NCD; ++kc) {
+    int c[3], d[3];
+    for (int t = 0; t < 3; ++t) { c[t] = 0; d[t] = 0; }
+    // powers of components kc / ND and kc % ND
+    auto pows = [](int l, int k, int* p) {
+      int i = l, off = 0;
+      while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
+      p[0] = i; p[2] = k - off; p[1] = l - p[0] - p[2];
+    };
+    pows(lc, kc / ND, c); pows(ld, kc % ND, d);
+    ket += (double)(c[0] + d[0] + 1) * (c[1] + d[1] + 1) * (c[2] + d[2] + 1) * (3 + 2.0 * NHAB);
+  }
+  ClassFlops f;
+  f.per_pq = nchunk * (boys + rrec + ecd + 12.0) + ket;
+  double bra = 0;
+  for (int ab = 0; ab < NAB; ++ab) {
+    int a[3], bb[3];
+    auto pows = [](int l, int k, int* p) {
+      int i = l, off = 0;
+      while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
+      p[0] = i; p[2] = k - off; p[1] = l - p[0] - p[2];
+    };
+    pows(la, ab / NB, a); pows(lb, ab % NB, bb);
+    bra += (double)(a[0] + bb[0] + 1) * (a[1] + bb[1] + 1) * (a[2] + bb[2] + 1) * (3.0 * nchunk + 2.0 * NCD);
+  }
+  f.per_bra = bra + nchunk * 3 * 3.0 * (la + 1) * (lb + 1) * (la + lb + 1);
+  f.per_q = 12.0 * NAB * NCD;
+  return f;
 }
 
 // Exclusive prefix sums of the per-bra counts of every (class pair, band):
@@ -374,27 +480,56 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
 
 // ---------------------------------------------------------------------------
 // a7: spherical <-> Cartesian transforms (block-diagonal T, rows m, columns
-// Cartesian components): D_cart = T^T D T and X_out = T sym(X_cart) T^T.
-__global__ void k_d_to_cart(int nc, int nbf, int spherical, const int* __restrict__ cshell,
-                            const int* __restrict__ ccomp, const int* __restrict__ shell_l,
-                            const int* __restrict__ shell_soff, const double* __restrict__ D, double* Dc,
-                            float* Dc32) {
+// Cartesian components), on packed per-molecule blocks:
+//   D_cart = T^T D T,   X_out = T sym(X_cart) T^T,   sym(X) = (X + X^T) / 2.
+struct XformArgs {
+  int nmol, spherical;
+  const long long* cbase;   // [nmol+1] packed Cartesian offsets
+  const long long* obase;   // [nmol+1] packed output offsets
+  const int* nc;            // [nmol]
+  const int* nbf;           // [nmol]
+  const int* cf_off;        // [nmol+1] Cartesian function offsets
+  const int* f_off;         // [nmol+1] output function offsets
+  const int* cshell;        // Cartesian function -> shell
+  const int* ccomp;
+  const int* fshell;        // output function -> shell
+  const int* fcomp;
+  const int* shell_l;
+  const int* shell_coff;    // local Cartesian offset of a shell inside its molecule
+  const int* shell_soff;    // local output offset
+};
+
+__device__ __forceinline__ int find_mol(const long long* base, int nmol, long long g) {
+  int lo = 0, hi = nmol;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (base[mid] <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_d_to_cart(XformArgs x, long long total, const double* __restrict__ D, double* Dc, float* Dc32) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)nc * nc) return;
-  const int i = (int)(g / nc), j = (int)(g % nc);
+  if (g >= total) return;
+  const int m = find_mol(x.cbase, x.nmol, g);
+  const long long loc = g - x.cbase[m];
+  const int nc = x.nc[m], nb = x.nbf[m];
+  const int i = (int)(loc / nc), j = (int)(loc % nc);
+  const double* Dm = D + x.obase[m];
   double v;
-  if (!spherical) {
-    v = D[(long long)i * nbf + j];
+  if (!x.spherical) {
+    v = Dm[(long long)i * nb + j];
   } else {
-    const int sa = cshell[i], sb = cshell[j], ka = ccomp[i], kb = ccomp[j];
-    const int la = shell_l[sa], lb = shell_l[sb];
-    const int oa = shell_soff[sa], ob = shell_soff[sb];
+    const int gi = x.cf_off[m] + i, gj = x.cf_off[m] + j;
+    const int sa = x.cshell[gi], sb = x.cshell[gj], ka = x.ccomp[gi], kb = x.ccomp[gj];
+    const int la = x.shell_l[sa], lb = x.shell_l[sb];
+    const int oa = x.shell_soff[sa], ob = x.shell_soff[sb];
     v = 0.0;
-    for (int m = 0; m < 2 * la + 1; ++m) {
-      const double ta = c_sph[la][m][ka];
+    for (int mm = 0; mm < 2 * la + 1; ++mm) {
+      const double ta = c_sph[la][mm][ka];
       if (ta == 0.0) continue;
       double s = 0.0;
-      for (int mm = 0; mm < 2 * lb + 1; ++mm) s += c_sph[lb][mm][kb] * D[(long long)(oa + m) * nbf + ob + mm];
+      for (int mn = 0; mn < 2 * lb + 1; ++mn) s += c_sph[lb][mn][kb] * Dm[(long long)(oa + mm) * nb + ob + mn];
       v += ta * s;
     }
   }
@@ -402,21 +537,25 @@ __global__ void k_d_to_cart(int nc, int nbf, int spherical, const int* __restric
   Dc32[g] = (float)v;
 }
 
-__global__ void k_from_cart(int nc, int nbf, int spherical, const int* __restrict__ fshell,
-                            const int* __restrict__ fcomp, const int* __restrict__ shell_l,
-                            const int* __restrict__ shell_coff, const double* __restrict__ Jc,
+__global__ void k_from_cart(XformArgs x, long long total, const double* __restrict__ Jc,
                             const double* __restrict__ Kc, double* J, double* K) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)nbf * nbf) return;
-  const int I = (int)(g / nbf), Jn = (int)(g % nbf);
-  if (!spherical) {
-    J[g] = 0.5 * (Jc[(long long)I * nc + Jn] + Jc[(long long)Jn * nc + I]);
-    K[g] = 0.5 * (Kc[(long long)I * nc + Jn] + Kc[(long long)Jn * nc + I]);
+  if (g >= total) return;
+  const int m = find_mol(x.obase, x.nmol, g);
+  const long long loc = g - x.obase[m];
+  const int nc = x.nc[m], nb = x.nbf[m];
+  const int I = (int)(loc / nb), Jn = (int)(loc % nb);
+  const double* Jm = Jc + x.cbase[m];
+  const double* Km = Kc + x.cbase[m];
+  if (!x.spherical) {
+    J[g] = 0.5 * (Jm[(long long)I * nc + Jn] + Jm[(long long)Jn * nc + I]);
+    K[g] = 0.5 * (Km[(long long)I * nc + Jn] + Km[(long long)Jn * nc + I]);
     return;
   }
-  const int sa = fshell[I], sb = fshell[Jn], ma = fcomp[I], mb = fcomp[Jn];
-  const int la = shell_l[sa], lb = shell_l[sb];
-  const int oa = shell_coff[sa], ob = shell_coff[sb];
+  const int gi = x.f_off[m] + I, gj = x.f_off[m] + Jn;
+  const int sa = x.fshell[gi], sb = x.fshell[gj], ma = x.fcomp[gi], mb = x.fcomp[gj];
+  const int la = x.shell_l[sa], lb = x.shell_l[sb];
+  const int oa = x.shell_coff[sa], ob = x.shell_coff[sb];
   double vj = 0.0, vk = 0.0;
   for (int ka = 0; ka < ncart(la); ++ka) {
     const double ta = c_sph[la][ma][ka];
@@ -424,9 +563,9 @@ __global__ void k_from_cart(int nc, int nbf, int spherical, const int* __restric
     double sj = 0.0, sk = 0.0;
     for (int kb = 0; kb < ncart(lb); ++kb) {
       const double tb = c_sph[lb][mb][kb];
-      const long long x = (long long)(oa + ka) * nc + ob + kb, y = (long long)(ob + kb) * nc + oa + ka;
-      sj += tb * (Jc[x] + Jc[y]);
-      sk += tb * (Kc[x] + Kc[y]);
+      const long long p = (long long)(oa + ka) * nc + ob + kb, q = (long long)(ob + kb) * nc + oa + ka;
+      sj += tb * (Jm[p] + Jm[q]);
+      sk += tb * (Km[p] + Km[q]);
     }
     vj += ta * sj;
     vk += ta * sk;
@@ -435,11 +574,15 @@ __global__ void k_from_cart(int nc, int nbf, int spherical, const int* __restric
   K[g] = 0.5 * vk;
 }
 
-// a8: E = 1/2 sum D J - 1/4 sum D K (block reduction, one atomic per block)
-__global__ void k_energy(long long n, const double* __restrict__ D, const double* __restrict__ J,
-                         const double* __restrict__ K, double* E) {
+// a8: E = 1/2 sum D J - 1/4 sum D K over one molecule's block (one block of
+// threads per molecule, grid-stride inside the block).
+__global__ void k_energy(const long long* __restrict__ obase, const double* __restrict__ D,
+                         const double* __restrict__ J, const double* __restrict__ K, double* E) {
+  const int m = blockIdx.y;
+  const long long lo = obase[m], hi = obase[m + 1];
   double s = 0.0;
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x)
+  for (long long g = lo + (long long)blockIdx.x * blockDim.x + threadIdx.x; g < hi;
+       g += (long long)gridDim.x * blockDim.x)
     s += D[g] * (0.5 * J[g] - 0.25 * K[g]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   __shared__ double ws[32];
@@ -448,21 +591,24 @@ __global__ void k_energy(long long n, const double* __restrict__ D, const double
   if (threadIdx.x < 32) {
     s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) atomicAdd(E, s);
+    if (threadIdx.x == 0) atomicAdd(E + m, s);
   }
 }
 
-// D validation: max|D|, max|D - D^T| and a non-finite flag (no trap).
-__global__ void k_check_d(int n, const double* __restrict__ D, double* scal, int* status) {
+// D validation over the packed blocks: max|D|, max|D - D^T|, non-finite flag.
+__global__ void k_check_d(XformArgs x, long long total, const double* __restrict__ D, double* scal, int* status) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0, d = 0.0;
   int bad = 0;
-  if (g < (long long)n * n) {
-    const int i = (int)(g / n), j = (int)(g % n);
-    const double x = D[g], y = D[(long long)j * n + i];
-    if (!isfinite(x)) bad = 1;
-    a = fabs(x);
-    d = fabs(x - y);
+  if (g < total) {
+    const int m = find_mol(x.obase, x.nmol, g);
+    const long long loc = g - x.obase[m];
+    const int nb = x.nbf[m];
+    const int i = (int)(loc / nb), j = (int)(loc % nb);
+    const double v = D[g], w = D[x.obase[m] + (long long)j * nb + i];
+    if (!isfinite(v)) bad = 1;
+    a = fabs(v);
+    d = fabs(v - w);
   }
   for (int o = 16; o > 0; o >>= 1) {
     a = fmax(a, __shfl_down_sync(0xffffffffu, a, o));
@@ -477,45 +623,63 @@ __global__ void k_check_d(int n, const double* __restrict__ D, double* scal, int
   }
 }
 
-static int grid_for(int threads_per_block, int blocks_per_sm) {
+static int num_sms() {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  (void)threads_per_block;
-  return sms * blocks_per_sm;
+  return sms;
+}
+
+static XformArgs xform_args(const adft_basis* b) {
+  XformArgs x;
+  x.nmol = b->nmol; x.spherical = b->spherical;
+  x.cbase = b->d_mol_cbase; x.obase = b->d_mol_obase; x.nc = b->d_mol_nc; x.nbf = b->d_mol_nbf;
+  x.cf_off = b->d_mol_cf_off; x.f_off = b->d_mol_f_off;
+  x.cshell = b->d_cfunc_shell; x.ccomp = b->d_cfunc_comp; x.fshell = b->d_func_shell; x.fcomp = b->d_func_comp;
+  x.shell_l = b->d_shell_l; x.shell_coff = b->d_shell_coff; x.shell_soff = b->d_shell_soff;
+  return x;
 }
 
 // ---------------------------------------------------------------------------
-// one J/K build into the handle's Cartesian accumulators
+// one call: validation, D -> Cartesian, screening and work lists
 
 static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStream_t s) {
   Workspace& w = b->ws;
-  const long long nc2 = (long long)b->ncart * b->ncart;
+  b->ev_valid = 0;
+  ADFT_CUDA(cudaEventRecord(b->ev[0], s));
+  const long long nc2 = b->mol_cbase[b->nmol], nb2 = b->mol_obase[b->nmol];
   const int T256 = 256;
+  const XformArgs x = xform_args(b);
   ADFT_CUDA(cudaMemsetAsync(w.status, 0, sizeof(int), s));
   ADFT_CUDA(cudaMemsetAsync(w.scal, 0, 4 * sizeof(double), s));
   if (o->check) {
-    const long long nb2 = (long long)b->nbf * b->nbf;
-    k_check_d<<<(unsigned)((nb2 + T256 - 1) / T256), T256, 0, s>>>(b->nbf, D, w.scal, w.status);
+    k_check_d<<<(unsigned)((nb2 + T256 - 1) / T256), T256, 0, s>>>(x, nb2, D, w.scal, w.status);
     ADFT_CUDA(cudaGetLastError());
   }
-  k_d_to_cart<<<(unsigned)((nc2 + T256 - 1) / T256), T256, 0, s>>>(b->ncart, b->nbf, b->spherical, b->d_cfunc_shell,
-                                                                  b->d_cfunc_comp, b->d_shell_l, b->d_shell_soff, D,
-                                                                  w.Dc, w.Dc32);
+  k_d_to_cart<<<(unsigned)((nc2 + T256 - 1) / T256), T256, 0, s>>>(x, nc2, D, w.Dc, w.Dc32);
   ADFT_CUDA(cudaGetLastError());
   ADFT_CUDA(cudaMemsetAsync(w.Jc, 0, nc2 * sizeof(double), s));
   ADFT_CUDA(cudaMemsetAsync(w.Kc, 0, nc2 * sizeof(double), s));
-  ADFT_CUDA(cudaMemsetAsync(w.counters, 0, 2 * NCP * sizeof(unsigned long long), s));
+  ADFT_CUDA(cudaMemsetAsync(w.counters, 0, 4 * NCP * sizeof(unsigned long long), s));
   ADFT_CUDA(cudaMemsetAsync(w.stats, 0, 8 * sizeof(unsigned long long), s));
 
   ScreenArgs sa;
   memcpy(sa.cls_first, b->cls_first, sizeof(sa.cls_first));
   memcpy(sa.cnt_off, b->cnt_off, sizeof(sa.cnt_off));
+  sa.nmol = b->nmol;
+  sa.seg_first = b->d_seg_first;
+  sa.pair_mol = b->nmol > 1 ? b->d_pair_mol : nullptr;
   sa.Q = b->d_pair_Q; sa.ppn = b->d_pair_ppn; sa.cumppn = b->d_cumppn;
   sa.thresh = o->thresh;
   sa.mixed = (o->precision == ADFT_PREC_MIXED);
   sa.split = sa.mixed ? o->split : 0.0;
-  sa.cnt64 = w.cnt64; sa.cnt32 = w.cnt32; sa.stats = w.stats;
+  sa.cnt64 = w.cnt64; sa.cnt32 = w.cnt32; sa.kst64 = w.kst64; sa.kst32 = w.kst32; sa.stats = w.stats;
+  for (int X = 0; X < NCLS; ++X)
+    for (int Y = 0; Y <= X; ++Y) {
+      const ClassFlops f = class_flops(cls_la(X), cls_lb(X), cls_la(Y), cls_lb(Y));
+      const int cp = cp_index(X, Y);
+      sa.f_pq[cp] = (float)f.per_pq; sa.f_bra[cp] = (float)f.per_bra; sa.f_q[cp] = (float)f.per_q;
+    }
   if (b->npair > 0) {
     k_screen<<<(b->npair + T256 - 1) / T256, T256, 0, s>>>(sa, b->npair);
     ADFT_CUDA(cudaGetLastError());
@@ -531,8 +695,8 @@ static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStrea
   sc.cnt64 = w.cnt64; sc.cnt32 = w.cnt32; sc.pre64 = w.pre64; sc.pre32 = w.pre32;
   k_scan<<<2 * NCP, 1024, 0, s>>>(sc);
   ADFT_CUDA(cudaGetLastError());
+  ADFT_CUDA(cudaEventRecord(b->ev[1], s));
   b->last_stream = s;
-  b->last_prec = o->precision;
   return ADFT_OK;
 }
 
@@ -546,41 +710,70 @@ static JKLaunch base_launch(adft_basis* b) {
   return L;
 }
 
-// Launch one kernel per class pair and band; fn(X, Y, launch, band) issues it.
+// Launch one kernel per class pair and band, all FP64 kernels first, then the
+// FP32 ones; events ev[2], ev[3] close the two groups.  pass selects the work
+// counters (0: J/K, 1: gradient after J/K in the same call).
 template <typename Fn>
-static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, Fn fn) {
+static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cudaStream_t s, int pass, Fn fn) {
   Workspace& w = b->ws;
-  for (int X = NCLS - 1; X >= 0; --X)
-    for (int Y = X; Y >= 0; --Y) {
-      const int nX = b->cls_first[X + 1] - b->cls_first[X];
-      const int nY = b->cls_first[Y + 1] - b->cls_first[Y];
-      if (nX == 0 || nY == 0) continue;
-      const int cp = cp_index(X, Y);
-      L.bra_first = b->cls_first[X]; L.nbra = nX; L.ket_first = b->cls_first[Y];
-      L.same_class = (X == Y);
-      L.prefix = w.pre64 + b->pre_off[cp];
-      L.ket_start = nullptr;
-      L.counter = w.counters + 2 * cp;
-      cudaError_t e = fn(X, Y, L, 0);
-      if (e != cudaSuccess) { set_error(std::string("fp64 launch: ") + cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
-      if (o->precision == ADFT_PREC_MIXED) {
-        L.prefix = w.pre32 + b->pre_off[cp];
-        L.ket_start = w.cnt64 + b->cnt_off[cp];
-        L.counter = w.counters + 2 * cp + 1;
-        e = fn(X, Y, L, 1);
-        if (e != cudaSuccess) { set_error(std::string("fp32 launch: ") + cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
+  for (int band = 0; band < (o->precision == ADFT_PREC_MIXED ? 2 : 1); ++band) {
+    for (int X = NCLS - 1; X >= 0; --X)
+      for (int Y = X; Y >= 0; --Y) {
+        const int nX = b->cls_first[X + 1] - b->cls_first[X];
+        const int nY = b->cls_first[Y + 1] - b->cls_first[Y];
+        if (nX == 0 || nY == 0) continue;
+        const int cp = cp_index(X, Y);
+        L.bra_first = b->cls_first[X]; L.nbra = nX; L.ket_first = b->cls_first[Y];
+        L.same_class = (X == Y);
+        L.prefix = (band ? w.pre32 : w.pre64) + b->pre_off[cp];
+        L.ket_start = (band ? w.kst32 : w.kst64) + b->cnt_off[cp];
+        L.counter = w.counters + 2 * NCP * pass + 2 * cp + band;
+        const int grid = b->sms * b->tune_blocks[band][cp];
+        cudaError_t e = fn(X, Y, L, band, grid);
+        if (e != cudaSuccess) {
+          set_error(std::string(band ? "fp32" : "fp64") + " launch: " + cudaGetErrorString(e));
+          return ADFT_ERR_CUDA;
+        }
       }
-    }
+    ADFT_CUDA(cudaEventRecord(b->ev[2 + band], s));
+  }
+  if (o->precision != ADFT_PREC_MIXED) ADFT_CUDA(cudaEventRecord(b->ev[3], s));
   return ADFT_OK;
 }
 
 static int run_jk(adft_basis* b, const double* D, const adft_opts* o, cudaStream_t s) {
   int st = prepare(b, D, o, s);
   if (st) return st;
-  const int grid64 = grid_for(128, 4), grid32 = grid_for(128, 8);
-  return for_each_class_pair(b, o, base_launch(b), [&](int X, int Y, const JKLaunch& L, int band) {
-    return band == 0 ? launch_jk_fp64(X, Y, L, grid64, s) : launch_jk_fp32(X, Y, L, grid32, s);
+  return for_each_class_pair(b, o, base_launch(b), s, 0, [&](int X, int Y, const JKLaunch& L, int band, int grid) {
+    return band == 0 ? launch_jk_fp64(X, Y, L, grid, s) : launch_jk_fp32(X, Y, L, grid, s);
   });
+}
+
+static int run_grad(adft_basis* b, const adft_opts* o, cudaStream_t s, double* grad, int pass) {
+  ADFT_CUDA(cudaMemsetAsync(grad, 0, 3 * sizeof(double) * b->natom, s));
+  return for_each_class_pair(b, o, base_launch(b), s, pass, [&](int X, int Y, const JKLaunch& L, int band, int grid) {
+    GradLaunch g;
+    g.jk = L;
+    g.grad = grad;
+    return band == 0 ? launch_grad_fp64(X, Y, g, grid, s) : launch_grad_fp32(X, Y, g, grid, s);
+  });
+}
+
+static int output_jk(adft_basis* b, cudaStream_t s, double* J, double* K) {
+  const long long nb2 = b->mol_obase[b->nmol];
+  k_from_cart<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(xform_args(b), nb2, b->ws.Jc, b->ws.Kc, J, K);
+  ADFT_CUDA(cudaGetLastError());
+  return ADFT_OK;
+}
+
+static int output_energy(adft_basis* b, cudaStream_t s, const double* D, const double* J, const double* K,
+                         double* E) {
+  ADFT_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * b->nmol, s));
+  const long long per = b->mol_obase[b->nmol] / b->nmol;
+  const int bx = (int)std::min<long long>(std::max<long long>(1, per / (256 * 64)), (long long)b->sms * 4);
+  k_energy<<<dim3(bx, b->nmol), 256, 0, s>>>(b->d_mol_obase, D, J, K, E);
+  ADFT_CUDA(cudaGetLastError());
+  return ADFT_OK;
 }
 
 static int finish_check(adft_basis* b, const adft_opts* o, cudaStream_t s) {
@@ -591,7 +784,7 @@ static int finish_check(adft_basis* b, const adft_opts* o, cudaStream_t s) {
   ADFT_CUDA(cudaMemcpyAsync(scal, b->ws.scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
   ADFT_CUDA(cudaStreamSynchronize(s));
   if (st != 0) {
-    set_error(st == ADFT_ERR_NONFINITE ? "D holds NaN or Inf" : "device status set");
+    set_error(st == ADFT_ERR_NONFINITE ? "D holds NaN or Inf" : st == ADFT_ERR_ABORTED ? "aborted" : "device status set");
     return st;
   }
   if (scal[2] > 1e-12 * scal[1]) {
@@ -625,6 +818,248 @@ static int set_device(adft_basis* b) {
   return ADFT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// basis construction (one molecule or a batch of molecules)
+
+struct HostMol {
+  const double* xyz;
+  int natom;
+  std::vector<int> l, atom, nprim;        // per shell, atom local to the molecule
+  std::vector<double> exps, ncoefs;       // per primitive, ncoefs = c_i N(a_i, l)
+};
+
+static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int spherical) {
+  int st = ADFT_OK;
+  b->nmol = (int)mols.size();
+  b->spherical = spherical;
+  b->sms = 0;
+  if (cudaGetDevice(&b->device) != cudaSuccess) { set_error("no CUDA device"); return ADFT_ERR_CUDA; }
+  cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (b->sms <= 0) b->sms = 152;
+  // ---- shells and per-molecule offsets
+  b->mol_atom_off.assign(1, 0); b->mol_shell_off.assign(1, 0); b->mol_cf_off.assign(1, 0); b->mol_f_off.assign(1, 0);
+  b->mol_cbase.assign(1, 0); b->mol_obase.assign(1, 0);
+  int poff = 0;
+  for (int m = 0; m < b->nmol; ++m) {
+    const HostMol& M = mols[m];
+    b->xyz.insert(b->xyz.end(), M.xyz, M.xyz + 3 * M.natom);
+    int coff = 0, soff = 0, q = 0;
+    for (size_t s = 0; s < M.l.size(); ++s) {
+      const int l = M.l[s];
+      b->shell_l.push_back(l);
+      b->shell_atom.push_back(b->mol_atom_off[m] + M.atom[s]);
+      b->shell_nprim.push_back(M.nprim[s]);
+      b->shell_poff.push_back(poff);
+      b->shell_coff.push_back(coff);
+      b->shell_soff.push_back(spherical ? soff : coff);
+      b->shell_mol.push_back(m);
+      for (int i = 0; i < M.nprim[s]; ++i) {
+        b->exps.push_back(M.exps[q + i]);
+        b->ncoefs.push_back(M.ncoefs[q + i]);
+      }
+      q += M.nprim[s];
+      poff += M.nprim[s];
+      coff += ncart(l);
+      soff += 2 * l + 1;
+    }
+    const int nbf = spherical ? soff : coff;
+    b->mol_nc.push_back(coff);
+    b->mol_nbf.push_back(nbf);
+    b->mol_atom_off.push_back(b->mol_atom_off[m] + M.natom);
+    b->mol_shell_off.push_back(b->mol_shell_off[m] + (int)M.l.size());
+    b->mol_cf_off.push_back(b->mol_cf_off[m] + coff);
+    b->mol_f_off.push_back(b->mol_f_off[m] + nbf);
+    b->mol_cbase.push_back(b->mol_cbase[m] + (long long)coff * coff);
+    b->mol_obase.push_back(b->mol_obase[m] + (long long)nbf * nbf);
+  }
+  b->natom = b->mol_atom_off[b->nmol];
+  b->nshell = b->mol_shell_off[b->nmol];
+  b->ncart = b->mol_cf_off[b->nmol];
+  b->nbf = b->mol_f_off[b->nmol];
+
+  // ---- pairs inside each molecule: class-major, molecule-minor (l_a >= l_b; ties: larger index first)
+  std::vector<std::vector<std::vector<std::pair<int, int>>>> by(NCLS, std::vector<std::vector<std::pair<int, int>>>(b->nmol));
+  for (int m = 0; m < b->nmol; ++m)
+    for (int a = b->mol_shell_off[m]; a < b->mol_shell_off[m + 1]; ++a)
+      for (int c = b->mol_shell_off[m]; c <= a; ++c) {
+        int x = a, y = c;
+        if (b->shell_l[y] > b->shell_l[x]) std::swap(x, y);
+        by[cls_of(b->shell_l[x], b->shell_l[y])][m].push_back({x, y});
+      }
+  std::vector<int> pa, pb, pmol;
+  b->seg_first.assign(NCLS * (b->nmol + 1), 0);
+  for (int X = 0; X < NCLS; ++X) {
+    b->cls_first[X] = (int)pa.size();
+    for (int m = 0; m < b->nmol; ++m) {
+      b->seg_first[X * (b->nmol + 1) + m] = (int)pa.size();
+      for (auto& pr : by[X][m]) { pa.push_back(pr.first); pb.push_back(pr.second); pmol.push_back(m); }
+    }
+    b->seg_first[X * (b->nmol + 1) + b->nmol] = (int)pa.size();
+  }
+  b->cls_first[NCLS] = (int)pa.size();
+  b->npair = (int)pa.size();
+
+  st = boys_tables(&b->boys64, &b->boys32);
+  if (st != cudaSuccess) { set_error("Boys table upload failed"); return ADFT_ERR_CUDA; }
+  {
+    double h_sph[LMAX + 1][2 * LMAX + 1][SPH_MAXC];
+    sph_coefficients(h_sph);
+    if (cudaMemcpyToSymbol(c_sph, h_sph, sizeof(h_sph)) != cudaSuccess) {
+      set_error("spherical coefficient upload failed");
+      return ADFT_ERR_CUDA;
+    }
+  }
+  if ((st = upload(b, &b->d_shell_l, b->shell_l)) || (st = upload(b, &b->d_shell_atom, b->shell_atom)) ||
+      (st = upload(b, &b->d_shell_coff, b->shell_coff)) || (st = upload(b, &b->d_shell_soff, b->shell_soff)) ||
+      (st = upload(b, &b->d_shell_nprim, b->shell_nprim)) || (st = upload(b, &b->d_shell_poff, b->shell_poff)) ||
+      (st = upload(b, &b->d_xyz, b->xyz)) || (st = upload(b, &b->d_exps, b->exps)) ||
+      (st = upload(b, &b->d_ncoefs, b->ncoefs)) || (st = upload(b, &b->d_mol_nc, b->mol_nc)) ||
+      (st = upload(b, &b->d_mol_nbf, b->mol_nbf)) || (st = upload(b, &b->d_mol_cf_off, b->mol_cf_off)) ||
+      (st = upload(b, &b->d_mol_f_off, b->mol_f_off)) || (st = upload(b, &b->d_mol_cbase, b->mol_cbase)) ||
+      (st = upload(b, &b->d_mol_obase, b->mol_obase)) || (st = upload(b, &b->d_seg_first, b->seg_first)))
+    return st;
+  {
+    std::vector<int> fs, fc, cs, cc;
+    for (int s = 0; s < b->nshell; ++s) {
+      const int l = b->shell_l[s];
+      for (int k = 0; k < ncart(l); ++k) { cs.push_back(s); cc.push_back(k); }
+      const int nf = spherical ? 2 * l + 1 : ncart(l);
+      for (int k = 0; k < nf; ++k) { fs.push_back(s); fc.push_back(k); }
+    }
+    if ((st = upload(b, &b->d_func_shell, fs)) || (st = upload(b, &b->d_func_comp, fc)) ||
+        (st = upload(b, &b->d_cfunc_shell, cs)) || (st = upload(b, &b->d_cfunc_comp, cc)))
+      return st;
+  }
+
+  // ---- a1/a2: pair data with every primitive pair, bounds Q_ab and Q_p;
+  // then sort each (class, molecule) segment by Q descending, drop primitive
+  // pairs with Q_p * max(Q_p) <= PRIM_EPS and rebuild in that order.
+  auto build = [&](const std::vector<int>& A, const std::vector<int>& B, const std::vector<int>& src,
+                   const std::vector<int>& ppoff, const std::vector<int>& ppn, bool first, int* pp_pair_dev) -> int {
+    const long long tot = (long long)src.size();
+    b->npp = tot;
+    int r;
+    if (first) {
+      if ((r = dalloc(b, &b->d_pair_a, A.size())) || (r = dalloc(b, &b->d_pair_b, A.size())) ||
+          (r = dalloc(b, &b->d_pair_ppoff, A.size())) || (r = dalloc(b, &b->d_pair_ppn, A.size())) ||
+          (r = dalloc(b, &b->d_pair_Q, A.size())) || (r = dalloc(b, &b->d_pair_AB, 3 * A.size())) ||
+          (r = dalloc(b, &b->d_pp64, (size_t)tot)) || (r = dalloc(b, &b->d_pp32, (size_t)tot)) ||
+          (r = dalloc(b, &b->d_ppw64, 2 * (size_t)tot)) || (r = dalloc(b, &b->d_ppw32, 2 * (size_t)tot)) ||
+          (r = dalloc(b, &b->d_pp_src, (size_t)tot)) || (r = dalloc(b, &b->d_o2p64, (size_t)tot)) ||
+          (r = dalloc(b, &b->d_o2p32, (size_t)tot)))
+        return r;
+    }
+    ADFT_CUDA(cudaMemcpy(b->d_pair_a, A.data(), A.size() * sizeof(int), cudaMemcpyHostToDevice));
+    ADFT_CUDA(cudaMemcpy(b->d_pair_b, B.data(), B.size() * sizeof(int), cudaMemcpyHostToDevice));
+    ADFT_CUDA(cudaMemcpy(b->d_pair_ppoff, ppoff.data(), ppoff.size() * sizeof(int), cudaMemcpyHostToDevice));
+    ADFT_CUDA(cudaMemcpy(b->d_pair_ppn, ppn.data(), ppn.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (tot > 0) ADFT_CUDA(cudaMemcpy(b->d_pp_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<double> ab(3 * A.size());
+    for (size_t i = 0; i < A.size(); ++i)
+      for (int k = 0; k < 3; ++k)
+        ab[3 * i + k] = b->xyz[3 * b->shell_atom[A[i]] + k] - b->xyz[3 * b->shell_atom[B[i]] + k];
+    ADFT_CUDA(cudaMemcpy(b->d_pair_AB, ab.data(), ab.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (tot > 0) {
+      const int T = 256;
+      k_build_pairs<<<(unsigned)((tot + T - 1) / T), T>>>((int)A.size(), b->d_pair_a, b->d_pair_b, b->d_pair_ppoff,
+                                                         b->d_pp_src, b->d_shell_atom, b->d_shell_poff, b->d_xyz,
+                                                         b->d_exps, b->d_ncoefs, tot, b->d_pp64, b->d_pp32,
+                                                         b->d_ppw64, b->d_ppw32, b->d_o2p64, b->d_o2p32,
+                                                         pp_pair_dev);
+      ADFT_CUDA(cudaGetLastError());
+    }
+    return ADFT_OK;
+  };
+  std::vector<int> src, ppoff(pa.size()), ppn(pa.size());
+  for (size_t i = 0; i < pa.size(); ++i) {
+    ppoff[i] = (int)src.size();
+    for (int x = 0; x < b->shell_nprim[pa[i]]; ++x)
+      for (int y = 0; y < b->shell_nprim[pb[i]]; ++y) src.push_back((x << 8) | y);
+    ppn[i] = (int)src.size() - ppoff[i];
+    if (src.size() > 0x7fffffffULL) { set_error("too many primitive pairs"); return ADFT_ERR_UNSUPPORTED; }
+  }
+  int* d_pp_pair = nullptr;
+  double* d_Qp = nullptr;
+  if ((st = dalloc(b, &d_pp_pair, src.size())) || (st = dalloc(b, &d_Qp, src.size()))) return st;
+  if ((st = build(pa, pb, src, ppoff, ppn, true, d_pp_pair))) return st;
+  {
+    BasisView v = view(b);
+    v.pair_mol = nullptr;  // bounds need no packed offsets
+    for (int X = 0; X < NCLS; ++X) {
+      const int n = b->cls_first[X + 1] - b->cls_first[X];
+      if (n == 0) continue;
+      cudaError_t e = launch_schwarz(X, v, b->cls_first[X], n, b->d_pair_Q, 0);
+      if (e != cudaSuccess) { set_error(std::string("schwarz: ") + cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
+      const int last = b->cls_first[X + 1] - 1;
+      const int npp_cls = ppoff[last] + ppn[last] - ppoff[b->cls_first[X]];
+      e = launch_prim_schwarz(X, v, b->cls_first[X], n, d_pp_pair, npp_cls, d_Qp, 0);
+      if (e != cudaSuccess) { set_error(std::string("prim schwarz: ") + cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
+    }
+    std::vector<double> Q(b->npair), Qp(src.size());
+    if (cudaMemcpy(Q.data(), b->d_pair_Q, Q.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (!Qp.empty() && cudaMemcpy(Qp.data(), d_Qp, Qp.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)) {
+      set_error(std::string("schwarz readback: ") + cudaGetErrorString(cudaGetLastError()));
+      return ADFT_ERR_CUDA;
+    }
+    const double qpmax = Qp.empty() ? 0.0 : *std::max_element(Qp.begin(), Qp.end());
+    std::vector<int> idx(b->npair);
+    std::iota(idx.begin(), idx.end(), 0);
+    for (int X = 0; X < NCLS; ++X)
+      for (int m = 0; m < b->nmol; ++m)
+        std::stable_sort(idx.begin() + b->seg_first[X * (b->nmol + 1) + m],
+                         idx.begin() + b->seg_first[X * (b->nmol + 1) + m + 1],
+                         [&](int i, int j) { return Q[i] > Q[j]; });
+    std::vector<int> sa(b->npair), sb(b->npair), nsrc, nppoff(b->npair), nppn(b->npair);
+    b->pair_Q.resize(b->npair);
+    b->npp_dense = (long long)src.size();
+    for (int i = 0; i < b->npair; ++i) {
+      const int o = idx[i];
+      sa[i] = pa[o]; sb[i] = pb[o]; b->pair_Q[i] = Q[o];
+      nppoff[i] = (int)nsrc.size();
+      for (int k = ppoff[o]; k < ppoff[o] + ppn[o]; ++k)
+        if (Qp[k] * qpmax > PRIM_EPS) nsrc.push_back(src[k]);
+      nppn[i] = (int)nsrc.size() - nppoff[i];
+    }
+    b->pair_a = sa; b->pair_b = sb;
+    if ((st = build(sa, sb, nsrc, nppoff, nppn, false, nullptr))) return st;
+    ADFT_CUDA(cudaMemcpy(b->d_pair_Q, b->pair_Q.data(), b->npair * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<long long> cum(b->npair + 1, 0);
+    for (int i = 0; i < b->npair; ++i) cum[i + 1] = cum[i] + nppn[i];
+    if ((st = upload(b, &b->d_cumppn, cum))) return st;
+    if ((st = upload(b, &b->d_pair_mol, pmol))) return st;  // pmol is unchanged by the in-segment sort
+  }
+  // ---- workspace
+  {
+    long long co = 0, po = 0;
+    for (int X = 0; X < NCLS; ++X)
+      for (int Y = 0; Y <= X; ++Y) {
+        const int cp = cp_index(X, Y);
+        const int nX = b->cls_first[X + 1] - b->cls_first[X];
+        b->cnt_off[cp] = co; b->pre_off[cp] = po;
+        co += nX; po += nX + 1;
+        b->tune_blocks[0][cp] = 4;
+        b->tune_blocks[1][cp] = 8;
+      }
+    Workspace& w = b->ws;
+    const size_t nc2 = (size_t)b->mol_cbase[b->nmol], nb2 = (size_t)b->mol_obase[b->nmol];
+    if ((st = dalloc(b, &w.Dc, nc2)) || (st = dalloc(b, &w.Dc32, nc2)) || (st = dalloc(b, &w.Jc, nc2)) ||
+        (st = dalloc(b, &w.Kc, nc2)) || (st = dalloc(b, &w.Jw, nb2)) || (st = dalloc(b, &w.Kw, nb2)) ||
+        (st = dalloc(b, &w.cnt64, (size_t)co)) || (st = dalloc(b, &w.cnt32, (size_t)co)) ||
+        (st = dalloc(b, &w.kst64, (size_t)co)) || (st = dalloc(b, &w.kst32, (size_t)co)) ||
+        (st = dalloc(b, &w.pre64, (size_t)po)) || (st = dalloc(b, &w.pre32, (size_t)po)) ||
+        (st = dalloc(b, &w.counters, 4 * NCP)) || (st = dalloc(b, &w.status, 4)) ||
+        (st = dalloc(b, &w.scal, 4)) || (st = dalloc(b, &w.Emol, (size_t)b->nmol)) || (st = dalloc(b, &w.stats, 8)))
+      return st;
+    ADFT_CUDA(cudaMemset(w.status, 0, 4 * sizeof(int)));
+  }
+  for (auto& e : b->ev) ADFT_CUDA(cudaEventCreate(&e));
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error(std::string("basis setup: ") + cudaGetErrorString(cudaGetLastError()));
+    return ADFT_ERR_CUDA;
+  }
+  return ADFT_OK;
+}
+
 }  // namespace adft
 
 using namespace adft;
@@ -634,7 +1069,7 @@ using namespace adft;
 
 extern "C" {
 
-const char* adft_version(void) { return "adft-gb300 0.1"; }
+const char* adft_version(void) { return "adft-gb300 0.2"; }
 
 const char* adft_status_string(int st) {
   switch (st) {
@@ -655,6 +1090,8 @@ const char* adft_last_error_message(void) { return g_last_error.c_str(); }
 
 void adft_basis_destroy(adft_basis* b) {
   if (!b) return;
+  for (auto& e : b->ev)
+    if (e) cudaEventDestroy(e);
   for (void* p : b->allocations) cudaFree(p);
   delete b;
 }
@@ -670,6 +1107,9 @@ int adft_basis_create(const double* atom_xyz, int natom, const adft_shell* shell
   if (spherical != 0 && spherical != 1) { set_error("spherical must be 0 or 1"); return ADFT_ERR_ARG; }
   for (int i = 0; i < 3 * natom; ++i)
     if (!isfinite(atom_xyz[i])) { set_error("atom_xyz holds a non-finite value"); return ADFT_ERR_ARG; }
+  HostMol M;
+  M.xyz = atom_xyz;
+  M.natom = natom;
   for (int s = 0; s < nshell; ++s) {
     const adft_shell& sh = shells[s];
     if (sh.atom < 0 || sh.atom >= natom || sh.l < 0 || sh.l > ADFT_LMAX || sh.nprim < 1 ||
@@ -680,175 +1120,23 @@ int adft_basis_create(const double* atom_xyz, int natom, const adft_shell* shell
       set_error(buf);
       return ADFT_ERR_ARG;
     }
-    for (int i = 0; i < sh.nprim; ++i)
+    double df = 1.0;
+    for (int k = 2 * sh.l - 1; k > 1; k -= 2) df *= k;
+    for (int i = 0; i < sh.nprim; ++i) {
       if (!(sh.exps[i] > 0.0) || !isfinite(sh.exps[i]) || !isfinite(sh.coefs[i])) {
         set_error("shell exponents must be finite and > 0, coefficients finite");
         return ADFT_ERR_ARG;
       }
+      const double a = sh.exps[i];
+      M.exps.push_back(a);
+      M.ncoefs.push_back(sh.coefs[i] * pow(2.0 * a / M_PI, 0.75) * pow(4.0 * a, 0.5 * sh.l) / sqrt(df));
+    }
+    M.l.push_back(sh.l); M.atom.push_back(sh.atom); M.nprim.push_back(sh.nprim);
   }
   adft_basis* b = new (std::nothrow) adft_basis();
   if (!b) { set_error("host allocation failed"); return ADFT_ERR_OOM; }
-  int st = ADFT_OK;
-  auto fail = [&](int code) { adft_basis_destroy(b); return code; };
-  if (cudaGetDevice(&b->device) != cudaSuccess) { set_error("no CUDA device"); return fail(ADFT_ERR_CUDA); }
-  b->natom = natom; b->nshell = nshell; b->spherical = spherical;
-  b->xyz.assign(atom_xyz, atom_xyz + 3 * natom);
-  int coff = 0, soff = 0, poff = 0;
-  for (int s = 0; s < nshell; ++s) {
-    const adft_shell& sh = shells[s];
-    b->shell_l.push_back(sh.l); b->shell_atom.push_back(sh.atom); b->shell_nprim.push_back(sh.nprim);
-    b->shell_poff.push_back(poff); b->shell_coff.push_back(coff); b->shell_soff.push_back(spherical ? soff : coff);
-    coff += ncart(sh.l); soff += 2 * sh.l + 1; poff += sh.nprim;
-    double df = 1.0;
-    for (int k = 2 * sh.l - 1; k > 1; k -= 2) df *= k;
-    for (int i = 0; i < sh.nprim; ++i) {
-      const double a = sh.exps[i];
-      const double N = pow(2.0 * a / M_PI, 0.75) * pow(4.0 * a, 0.5 * sh.l) / sqrt(df);
-      b->exps.push_back(a);
-      b->ncoefs.push_back(sh.coefs[i] * N);
-    }
-  }
-  b->ncart = coff;
-  b->nbf = spherical ? soff : coff;
-
-  // pairs grouped by class (la >= lb; ties in l: larger shell index first)
-  std::vector<std::vector<std::pair<int, int>>> by_cls(NCLS);
-  for (int a = 0; a < nshell; ++a)
-    for (int c = 0; c <= a; ++c) {
-      int x = a, y = c;
-      if (b->shell_l[y] > b->shell_l[x]) std::swap(x, y);
-      by_cls[cls_of(b->shell_l[x], b->shell_l[y])].push_back({x, y});
-    }
-  b->npair = nshell * (nshell + 1) / 2;
-  std::vector<int> pa, pb;
-  b->cls_first[0] = 0;
-  for (int X = 0; X < NCLS; ++X) {
-    for (auto& pr : by_cls[X]) { pa.push_back(pr.first); pb.push_back(pr.second); }
-    b->cls_first[X + 1] = (int)pa.size();
-  }
-
-  st = boys_tables(&b->boys64, &b->boys32);
-  if (st != cudaSuccess) { set_error("Boys table upload failed"); return fail(ADFT_ERR_CUDA); }
-  {
-    double h_sph[LMAX + 1][2 * LMAX + 1][SPH_MAXC];
-    sph_coefficients(h_sph);
-    if (cudaMemcpyToSymbol(c_sph, h_sph, sizeof(h_sph)) != cudaSuccess) {
-      set_error("spherical coefficient upload failed");
-      return fail(ADFT_ERR_CUDA);
-    }
-  }
-  if ((st = upload(b, &b->d_shell_l, b->shell_l)) || (st = upload(b, &b->d_shell_atom, b->shell_atom)) ||
-      (st = upload(b, &b->d_shell_coff, b->shell_coff)) || (st = upload(b, &b->d_shell_soff, b->shell_soff)) ||
-      (st = upload(b, &b->d_shell_nprim, b->shell_nprim)) || (st = upload(b, &b->d_shell_poff, b->shell_poff)) ||
-      (st = upload(b, &b->d_xyz, b->xyz)) || (st = upload(b, &b->d_exps, b->exps)) ||
-      (st = upload(b, &b->d_ncoefs, b->ncoefs)))
-    return fail(st);
-  // function maps
-  {
-    std::vector<int> fs, fc, cs, cc;
-    for (int s = 0; s < nshell; ++s) {
-      const int l = b->shell_l[s];
-      for (int k = 0; k < ncart(l); ++k) { cs.push_back(s); cc.push_back(k); }
-      const int nf = spherical ? 2 * l + 1 : ncart(l);
-      for (int k = 0; k < nf; ++k) { fs.push_back(s); fc.push_back(k); }
-    }
-    if ((st = upload(b, &b->d_func_shell, fs)) || (st = upload(b, &b->d_func_comp, fc)) ||
-        (st = upload(b, &b->d_cfunc_shell, cs)) || (st = upload(b, &b->d_cfunc_comp, cc)))
-      return fail(st);
-  }
-
-  // build pair data twice: once in class order to get Q, then in Q order
-  auto build = [&](const std::vector<int>& A, const std::vector<int>& B, bool first) -> int {
-    std::vector<int> ppoff(A.size()), ppn(A.size());
-    long long tot = 0;
-    for (size_t i = 0; i < A.size(); ++i) {
-      ppoff[i] = (int)tot;
-      ppn[i] = b->shell_nprim[A[i]] * b->shell_nprim[B[i]];
-      tot += ppn[i];
-    }
-    if (tot > 0x7fffffffLL) { set_error("too many primitive pairs"); return ADFT_ERR_UNSUPPORTED; }
-    b->npp = tot;
-    int r;
-    if (first) {
-      if ((r = dalloc(b, &b->d_pair_a, A.size())) || (r = dalloc(b, &b->d_pair_b, A.size())) ||
-          (r = dalloc(b, &b->d_pair_ppoff, A.size())) || (r = dalloc(b, &b->d_pair_ppn, A.size())) ||
-          (r = dalloc(b, &b->d_pair_Q, A.size())) || (r = dalloc(b, &b->d_pair_AB, 3 * A.size())) ||
-          (r = dalloc(b, &b->d_pp64, (size_t)tot)) || (r = dalloc(b, &b->d_pp32, (size_t)tot)) ||
-          (r = dalloc(b, &b->d_ppw64, 2 * (size_t)tot)) || (r = dalloc(b, &b->d_ppw32, 2 * (size_t)tot)))
-        return r;
-    }
-    ADFT_CUDA(cudaMemcpy(b->d_pair_a, A.data(), A.size() * sizeof(int), cudaMemcpyHostToDevice));
-    ADFT_CUDA(cudaMemcpy(b->d_pair_b, B.data(), B.size() * sizeof(int), cudaMemcpyHostToDevice));
-    ADFT_CUDA(cudaMemcpy(b->d_pair_ppoff, ppoff.data(), ppoff.size() * sizeof(int), cudaMemcpyHostToDevice));
-    ADFT_CUDA(cudaMemcpy(b->d_pair_ppn, ppn.data(), ppn.size() * sizeof(int), cudaMemcpyHostToDevice));
-    const int T = 256;
-    k_build_pairs<<<(unsigned)((tot + T - 1) / T), T>>>((int)A.size(), b->d_pair_a, b->d_pair_b, b->d_pair_ppoff,
-                                                       b->d_shell_atom, b->d_shell_nprim, b->d_shell_poff,
-                                                       b->d_xyz, b->d_exps, b->d_ncoefs, tot, b->d_pp64,
-                                                       b->d_pp32, b->d_pair_AB, b->d_ppw64, b->d_ppw32);
-    ADFT_CUDA(cudaGetLastError());
-    return ADFT_OK;
-  };
-  if ((st = build(pa, pb, true))) return fail(st);
-  // a2: Schwarz bounds on the device
-  {
-    BasisView v = view(b);
-    for (int X = 0; X < NCLS; ++X) {
-      const int n = b->cls_first[X + 1] - b->cls_first[X];
-      if (n == 0) continue;
-      cudaError_t e = launch_schwarz(X, v, b->cls_first[X], n, b->d_pair_Q, 0);
-      if (e != cudaSuccess) { set_error(std::string("schwarz: ") + cudaGetErrorString(e)); return fail(ADFT_ERR_CUDA); }
-    }
-    std::vector<double> Q(b->npair);
-    if (cudaMemcpy(Q.data(), b->d_pair_Q, Q.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      set_error(std::string("schwarz readback: ") + cudaGetErrorString(cudaGetLastError()));
-      return fail(ADFT_ERR_CUDA);
-    }
-    // sort each class by Q descending (stable), rebuild in that order
-    std::vector<int> idx(b->npair);
-    std::iota(idx.begin(), idx.end(), 0);
-    for (int X = 0; X < NCLS; ++X)
-      std::stable_sort(idx.begin() + b->cls_first[X], idx.begin() + b->cls_first[X + 1],
-                       [&](int i, int j) { return Q[i] > Q[j]; });
-    std::vector<int> sa(b->npair), sb(b->npair);
-    b->pair_Q.resize(b->npair);
-    for (int i = 0; i < b->npair; ++i) { sa[i] = pa[idx[i]]; sb[i] = pb[idx[i]]; b->pair_Q[i] = Q[idx[i]]; }
-    b->pair_a = sa; b->pair_b = sb;
-    if ((st = build(sa, sb, false))) return fail(st);
-    if (cudaMemcpy(b->d_pair_Q, b->pair_Q.data(), b->npair * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
-      set_error("Q upload failed");
-      return fail(ADFT_ERR_CUDA);
-    }
-    std::vector<long long> cum(b->npair + 1, 0);
-    for (int i = 0; i < b->npair; ++i) cum[i + 1] = cum[i] + (long long)b->shell_nprim[sa[i]] * b->shell_nprim[sb[i]];
-    if ((st = upload(b, &b->d_cumppn, cum))) return fail(st);
-  }
-  // workspace
-  {
-    long long co = 0, po = 0;
-    for (int X = 0; X < NCLS; ++X)
-      for (int Y = 0; Y <= X; ++Y) {
-        const int cp = cp_index(X, Y);
-        const int nX = b->cls_first[X + 1] - b->cls_first[X];
-        b->cnt_off[cp] = co; b->pre_off[cp] = po;
-        co += nX; po += nX + 1;
-      }
-    b->cnt_total = co; b->pre_total = po;
-    Workspace& w = b->ws;
-    const size_t nc2 = (size_t)b->ncart * b->ncart, nb2 = (size_t)b->nbf * b->nbf;
-    if ((st = dalloc(b, &w.Dc, nc2)) || (st = dalloc(b, &w.Dc32, nc2)) || (st = dalloc(b, &w.Jc, nc2)) ||
-        (st = dalloc(b, &w.Kc, nc2)) || (st = dalloc(b, &w.Jw, nb2)) || (st = dalloc(b, &w.Kw, nb2)) ||
-        (st = dalloc(b, &w.cnt64, (size_t)co)) || (st = dalloc(b, &w.cnt32, (size_t)co)) ||
-        (st = dalloc(b, &w.pre64, (size_t)po)) || (st = dalloc(b, &w.pre32, (size_t)po)) ||
-        (st = dalloc(b, &w.counters, 2 * NCP)) || (st = dalloc(b, &w.status, 4)) ||
-        (st = dalloc(b, &w.scal, 4)) || (st = dalloc(b, &w.stats, 8)))
-      return fail(st);
-    if (cudaMemset(w.status, 0, 4 * sizeof(int)) != cudaSuccess) { set_error("memset"); return fail(ADFT_ERR_CUDA); }
-  }
-  if (cudaDeviceSynchronize() != cudaSuccess) {
-    set_error(std::string("basis setup: ") + cudaGetErrorString(cudaGetLastError()));
-    return fail(ADFT_ERR_CUDA);
-  }
+  const int st = build_basis(b, std::vector<HostMol>{M}, spherical);
+  if (st) { adft_basis_destroy(b); return st; }
   *out = b;
   return ADFT_OK;
 }
@@ -869,6 +1157,7 @@ int adft_basis_dims(const adft_basis* b, int* natom, int* nshell, int* nc) {
 
 int adft_basis_schwarz(const adft_basis* b, double* Q) {
   if (!b || !Q) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  if (b->nmol != 1) { set_error("Schwarz bounds are reported for single-molecule bases"); return ADFT_ERR_ARG; }
   for (int i = 0; i < b->npair; ++i) {
     int x = b->pair_a[i], y = b->pair_b[i];
     if (y > x) std::swap(x, y);
@@ -877,43 +1166,53 @@ int adft_basis_schwarz(const adft_basis* b, double* Q) {
   return ADFT_OK;
 }
 
-int adft_jk_build(adft_basis* b, const double* D, const adft_opts* o, double* J, double* K) {
-  if (!b || !D || !J || !K) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+static int call_begin(adft_basis* b, const void* D, const adft_opts* o) {
+  if (!b || !D) { set_error("NULL argument"); return ADFT_ERR_ARG; }
   int st = check_opts(o);
   if (st) return st;
-  if ((st = set_device(b))) return st;
+  return set_device(b);
+}
+
+int adft_jk_build(adft_basis* b, const double* D, const adft_opts* o, double* J, double* K) {
+  int st = call_begin(b, D, o);
+  if (st) return st;
+  if (!J || !K) { set_error("NULL argument"); return ADFT_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)o->stream;
   if ((st = run_jk(b, D, o, s))) return st;
-  const long long nb2 = (long long)b->nbf * b->nbf;
-  k_from_cart<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(b->ncart, b->nbf, b->spherical, b->d_func_shell,
-                                                            b->d_func_comp, b->d_shell_l, b->d_shell_coff, b->ws.Jc,
-                                                            b->ws.Kc, J, K);
-  ADFT_CUDA(cudaGetLastError());
+  if ((st = output_jk(b, s, J, K))) return st;
+  ADFT_CUDA(cudaEventRecord(b->ev[4], s));
+  b->ev_valid = 1;
   return finish_check(b, o, s);
 }
 
 int adft_jk_energy(adft_basis* b, const double* D, const adft_opts* o, double* E, int E_on_device) {
-  if (!b || !D || !E) { set_error("NULL argument"); return ADFT_ERR_ARG; }
-  int st = check_opts(o);
+  int st = call_begin(b, D, o);
   if (st) return st;
-  if ((st = set_device(b))) return st;
+  if (!E) { set_error("NULL argument"); return ADFT_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)o->stream;
   if ((st = run_jk(b, D, o, s))) return st;
-  const long long nb2 = (long long)b->nbf * b->nbf;
-  k_from_cart<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(b->ncart, b->nbf, b->spherical, b->d_func_shell,
-                                                            b->d_func_comp, b->d_shell_l, b->d_shell_coff, b->ws.Jc,
-                                                            b->ws.Kc, b->ws.Jw, b->ws.Kw);
-  ADFT_CUDA(cudaGetLastError());
-  double* Ed = b->ws.scal;  // scal[0] holds the energy
-  ADFT_CUDA(cudaMemsetAsync(Ed, 0, sizeof(double), s));
-  k_energy<<<grid_for(256, 2), 256, 0, s>>>(nb2, D, b->ws.Jw, b->ws.Kw, Ed);
-  ADFT_CUDA(cudaGetLastError());
+  if ((st = output_jk(b, s, b->ws.Jw, b->ws.Kw))) return st;
+  if ((st = output_energy(b, s, D, b->ws.Jw, b->ws.Kw, b->ws.Emol))) return st;
+  ADFT_CUDA(cudaEventRecord(b->ev[4], s));
+  b->ev_valid = 1;
   if (E_on_device) {
-    ADFT_CUDA(cudaMemcpyAsync(E, Ed, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ADFT_CUDA(cudaMemcpyAsync(E, b->ws.Emol, sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else {
-    ADFT_CUDA(cudaMemcpyAsync(E, Ed, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ADFT_CUDA(cudaMemcpyAsync(E, b->ws.Emol, sizeof(double), cudaMemcpyDeviceToHost, s));
     ADFT_CUDA(cudaStreamSynchronize(s));
   }
+  return finish_check(b, o, s);
+}
+
+int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* o, double* grad) {
+  int st = call_begin(b, D, o);
+  if (st) return st;
+  if (!grad) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)o->stream;
+  if ((st = prepare(b, D, o, s))) return st;
+  if ((st = run_grad(b, o, s, grad, 0))) return st;
+  ADFT_CUDA(cudaEventRecord(b->ev[4], s));
+  b->ev_valid = 1;
   return finish_check(b, o, s);
 }
 
@@ -927,8 +1226,20 @@ int adft_jk_last_stats(adft_basis* b, adft_stats* out) {
   out->quartets_total = (int64_t)h[2];
   out->prim_quartets_fp64 = (int64_t)h[3];
   out->prim_quartets_fp32 = (int64_t)h[4];
-  out->flops_fp64 = 0.0;
-  out->flops_fp32 = 0.0;
+  out->flops_fp64 = (double)h[5];
+  out->flops_fp32 = (double)h[6];
+  return ADFT_OK;
+}
+
+int adft_jk_last_timings(adft_basis* b, double* ms) {
+  if (!b || !ms) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  if (!b->ev_valid) { set_error("no completed call to time"); return ADFT_ERR_ARG; }
+  ADFT_CUDA(cudaEventSynchronize(b->ev[4]));
+  for (int i = 0; i < 4; ++i) {
+    float t = 0.0f;
+    ADFT_CUDA(cudaEventElapsedTime(&t, b->ev[i], b->ev[i + 1]));
+    ms[i] = t;
+  }
   return ADFT_OK;
 }
 
@@ -947,35 +1258,199 @@ int adft_jk_status(adft_basis* b) {
   return st;
 }
 
-int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* o, double* grad) {
-  if (!b || !D || !grad) { set_error("NULL argument"); return ADFT_ERR_ARG; }
-  int st = check_opts(o);
+// ---- autotuner: blocks per SM of every class-pair kernel and band
+
+int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table, double* ms_out) {
+  int st = call_begin(b, D, o);
   if (st) return st;
-  if ((st = set_device(b))) return st;
   cudaStream_t s = (cudaStream_t)o->stream;
   if ((st = prepare(b, D, o, s))) return st;
-  ADFT_CUDA(cudaMemsetAsync(grad, 0, 3 * sizeof(double) * b->natom, s));
-  const int grid = grid_for(128, 4);
-  st = for_each_class_pair(b, o, base_launch(b), [&](int X, int Y, const JKLaunch& L, int band) {
-    GradLaunch g;
-    g.jk = L;
-    g.grad = grad;
-    return band == 0 ? launch_grad_fp64(X, Y, g, grid, s) : launch_grad_fp32(X, Y, g, grid, s);
-  });
-  if (st) return st;
-  return finish_check(b, o, s);
+  static const int cand[] = {1, 2, 4, 8, 16};
+  cudaEvent_t e0, e1;
+  ADFT_CUDA(cudaEventCreate(&e0));
+  ADFT_CUDA(cudaEventCreate(&e1));
+  if (ms_out)
+    for (int i = 0; i < 2 * NCP; ++i) ms_out[i] = 0.0;
+  for (int band = 0; band < (o->precision == ADFT_PREC_MIXED ? 2 : 1); ++band)
+    for (int X = NCLS - 1; X >= 0; --X)
+      for (int Y = X; Y >= 0; --Y) {
+        const int cp = cp_index(X, Y);
+        if (b->cls_first[X + 1] == b->cls_first[X] || b->cls_first[Y + 1] == b->cls_first[Y]) continue;
+        float best = 1e30f;
+        int best_c = b->tune_blocks[band][cp];
+        for (int c : cand) {
+          JKLaunch L = base_launch(b);
+          L.bra_first = b->cls_first[X]; L.nbra = b->cls_first[X + 1] - b->cls_first[X];
+          L.ket_first = b->cls_first[Y]; L.same_class = (X == Y);
+          L.prefix = (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp];
+          L.ket_start = (band ? b->ws.kst32 : b->ws.kst64) + b->cnt_off[cp];
+          L.counter = b->ws.counters + 2 * NCP + 2 * cp + band;
+          ADFT_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s));
+          ADFT_CUDA(cudaEventRecord(e0, s));
+          cudaError_t e = band == 0 ? launch_jk_fp64(X, Y, L, b->sms * c, s) : launch_jk_fp32(X, Y, L, b->sms * c, s);
+          if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
+          ADFT_CUDA(cudaEventRecord(e1, s));
+          ADFT_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.0f;
+          ADFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best * 0.97f) { best = ms; best_c = c; }
+        }
+        b->tune_blocks[band][cp] = best_c;
+        if (ms_out) ms_out[band * NCP + cp] = best;
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (table) memcpy(table, b->tune_blocks, sizeof(b->tune_blocks));
+  return ADFT_OK;
 }
 
+int adft_jk_plan(adft_basis* b, const double* D, const adft_opts* o, adft_stats* st, int64_t* quartets) {
+  int r = call_begin(b, D, o);
+  if (r) return r;
+  cudaStream_t s = (cudaStream_t)o->stream;
+  if ((r = prepare(b, D, o, s))) return r;
+  ADFT_CUDA(cudaStreamSynchronize(s));
+  if (quartets) {
+    for (int band = 0; band < 2; ++band)
+      for (int X = 0; X < NCLS; ++X)
+        for (int Y = 0; Y <= X; ++Y) {
+          const int cp = cp_index(X, Y);
+          const int nX = b->cls_first[X + 1] - b->cls_first[X];
+          long long v = 0;
+          ADFT_CUDA(cudaMemcpy(&v, (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp] + nX, sizeof(v),
+                               cudaMemcpyDeviceToHost));
+          quartets[band * NCP + cp] = v;
+        }
+  }
+  return st ? adft_jk_last_stats(b, st) : ADFT_OK;
+}
+
+int adft_set_tuning(adft_basis* b, const int* table) {
+  if (!b || !table) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  for (int i = 0; i < 2 * NCP; ++i)
+    if (table[i] < 1 || table[i] > 64) { set_error("blocks per SM must be in 1..64"); return ADFT_ERR_ARG; }
+  memcpy(b->tune_blocks, table, sizeof(b->tune_blocks));
+  return ADFT_OK;
+}
+
+// ---- batched form
+
 int adft_batch_create(adft_basis* const* mols, int nmol, adft_batch** out) {
-  (void)mols; (void)nmol; (void)out;
-  set_error("batched form not built yet");
-  return ADFT_ERR_UNSUPPORTED;
+  if (!out || !mols || nmol <= 0) { set_error("mols/out must be non-NULL and nmol > 0"); return ADFT_ERR_ARG; }
+  *out = nullptr;
+  std::vector<HostMol> H(nmol);
+  int spherical = -1, dev = -1;
+  for (int m = 0; m < nmol; ++m) {
+    const adft_basis* s = mols[m];
+    if (!s || s->nmol != 1) { set_error("every batch member must be a single-molecule basis"); return ADFT_ERR_ARG; }
+    if (spherical >= 0 && s->spherical != spherical) { set_error("mixed spherical/Cartesian bases"); return ADFT_ERR_ARG; }
+    if (dev >= 0 && s->device != dev) { set_error("bases on different devices"); return ADFT_ERR_ARG; }
+    spherical = s->spherical; dev = s->device;
+    HostMol& M = H[m];
+    M.xyz = s->xyz.data();
+    M.natom = s->natom;
+    M.l = s->shell_l; M.atom = s->shell_atom; M.nprim = s->shell_nprim;
+    M.exps = s->exps; M.ncoefs = s->ncoefs;
+  }
+  adft_batch* bt = new (std::nothrow) adft_batch();
+  if (!bt) { set_error("host allocation failed"); return ADFT_ERR_OOM; }
+  bt->b = new (std::nothrow) adft_basis();
+  if (!bt->b) { delete bt; set_error("host allocation failed"); return ADFT_ERR_OOM; }
+  const int st = build_basis(bt->b, H, spherical);
+  if (st) { adft_batch_destroy(bt); return st; }
+  *out = bt;
+  return ADFT_OK;
 }
-int adft_batch_offsets(const adft_batch*, int64_t*) { return ADFT_ERR_UNSUPPORTED; }
-int adft_batch_grad_offsets(const adft_batch*, int64_t*) { return ADFT_ERR_UNSUPPORTED; }
-int adft_batch_jk(adft_batch*, const double*, const adft_opts*, double*, double*, double*, double*) {
-  return ADFT_ERR_UNSUPPORTED;
+
+int adft_batch_offsets(const adft_batch* bt, int64_t* offsets) {
+  if (!bt || !offsets) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  for (int m = 0; m <= bt->b->nmol; ++m) offsets[m] = bt->b->mol_obase[m];
+  return ADFT_OK;
 }
-void adft_batch_destroy(adft_batch*) {}
+
+int adft_batch_grad_offsets(const adft_batch* bt, int64_t* offsets) {
+  if (!bt || !offsets) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  for (int m = 0; m <= bt->b->nmol; ++m) offsets[m] = 3LL * bt->b->mol_atom_off[m];
+  return ADFT_OK;
+}
+
+
+
+static int batch_sequence(adft_basis* b, const double* D, const adft_opts* o, cudaStream_t s, double* J, double* K,
+                          double* E, double* grad) {
+  int st = run_jk(b, D, o, s);
+  if (st) return st;
+  if ((st = output_jk(b, s, J, K))) return st;
+  if (E && (st = output_energy(b, s, D, J, K, E))) return st;
+  if (grad && (st = run_grad(b, o, s, grad, 1))) return st;
+  ADFT_CUDA(cudaEventRecord(b->ev[4], s));
+  return ADFT_OK;
+}
+
+int adft_batch_jk(adft_batch* bt, const double* D, const adft_opts* o, double* J, double* K, double* E,
+                  double* grad) {
+  if (!bt) { set_error("NULL batch"); return ADFT_ERR_ARG; }
+  adft_basis* b = bt->b;
+  int st = call_begin(b, D, o);
+  if (st) return st;
+  if (!J || !K) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)o->stream;
+  if (o->check || s == nullptr) {
+    // direct launches (validation needs a synchronisation; the legacy
+    // default stream cannot be captured)
+    if ((st = batch_sequence(b, D, o, s, J, K, E, grad))) return st;
+    b->ev_valid = 1;
+    return finish_check(b, o, s);
+  }
+  // one CUDA graph per (buffers, options): captured on first use, replayed after
+  auto key = std::make_tuple((const void*)D, (const void*)J, (const void*)K, (const void*)E, (const void*)grad,
+                             o->thresh, o->split, o->precision, (void*)s);
+  if (!bt->has_graph || bt->key != key) {
+    if (bt->exec) { cudaGraphExecDestroy(bt->exec); bt->exec = nullptr; }
+    if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+    bt->has_graph = false;
+    ADFT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    st = batch_sequence(b, D, o, s, J, K, E, grad);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    if (st) { if (g) cudaGraphDestroy(g); return st; }
+    if (ec != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(ec)); return ADFT_ERR_CUDA; }
+    bt->graph = g;
+    ADFT_CUDA(cudaGraphInstantiate(&bt->exec, bt->graph, 0));
+    bt->key = key;
+    bt->has_graph = true;
+  }
+  ADFT_CUDA(cudaGraphLaunch(bt->exec, s));
+  b->last_stream = s;
+  b->ev_valid = 1;
+  return ADFT_OK;
+}
+
+int adft_batch_last_stats(adft_batch* bt, adft_stats* st) {
+  if (!bt) { set_error("NULL batch"); return ADFT_ERR_ARG; }
+  return adft_jk_last_stats(bt->b, st);
+}
+
+int adft_batch_last_timings(adft_batch* bt, double* ms) {
+  if (!bt) { set_error("NULL batch"); return ADFT_ERR_ARG; }
+  return adft_jk_last_timings(bt->b, ms);
+}
+
+int adft_batch_autotune(adft_batch* bt, const double* D, const adft_opts* o, int* table, double* ms) {
+  if (!bt) { set_error("NULL batch"); return ADFT_ERR_ARG; }
+  if (bt->has_graph) {  // the captured graph holds the old launch shapes
+    cudaGraphExecDestroy(bt->exec); cudaGraphDestroy(bt->graph);
+    bt->exec = nullptr; bt->graph = nullptr; bt->has_graph = false;
+  }
+  return adft_autotune(bt->b, D, o, table, ms);
+}
+
+void adft_batch_destroy(adft_batch* bt) {
+  if (!bt) return;
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->graph) cudaGraphDestroy(bt->graph);
+  adft_basis_destroy(bt->b);
+  delete bt;
+}
 
 }  // extern "C"

@@ -61,12 +61,26 @@ struct ChunkPlan {
 template <typename T> struct Prec;
 template <> struct Prec<double> {
   static __device__ __forceinline__ const PrimPair<double>* pp(const BasisView& b) { return b.pp64; }
+  static __device__ __forceinline__ const double* o2p(const BasisView& b) { return b.pp_o2p64; }
+  static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
   static constexpr int BUDGET = 640;
 };
 template <> struct Prec<float> {
   static __device__ __forceinline__ const PrimPair<float>* pp(const BasisView& b) { return b.pp32; }
+  static __device__ __forceinline__ const float* o2p(const BasisView& b) { return b.pp_o2p32; }
+  static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
   static constexpr int BUDGET = 640;
 };
+
+// reciprocals 1/(2m+1), m < 32
+__constant__ static const double c_inv_odd64[32] = {
+    1.0 / 1, 1.0 / 3, 1.0 / 5, 1.0 / 7, 1.0 / 9, 1.0 / 11, 1.0 / 13, 1.0 / 15, 1.0 / 17, 1.0 / 19, 1.0 / 21,
+    1.0 / 23, 1.0 / 25, 1.0 / 27, 1.0 / 29, 1.0 / 31, 1.0 / 33, 1.0 / 35, 1.0 / 37, 1.0 / 39, 1.0 / 41,
+    1.0 / 43, 1.0 / 45, 1.0 / 47, 1.0 / 49, 1.0 / 51, 1.0 / 53, 1.0 / 55, 1.0 / 57, 1.0 / 59, 1.0 / 61, 1.0 / 63};
+__constant__ static const float c_inv_odd32[32] = {
+    1.f / 1, 1.f / 3, 1.f / 5, 1.f / 7, 1.f / 9, 1.f / 11, 1.f / 13, 1.f / 15, 1.f / 17, 1.f / 19, 1.f / 21,
+    1.f / 23, 1.f / 25, 1.f / 27, 1.f / 29, 1.f / 31, 1.f / 33, 1.f / 35, 1.f / 37, 1.f / 39, 1.f / 41,
+    1.f / 43, 1.f / 45, 1.f / 47, 1.f / 49, 1.f / 51, 1.f / 53, 1.f / 55, 1.f / 57, 1.f / 59, 1.f / 61, 1.f / 63};
 
 // ---------------------------------------------------------------------------
 // Boys function F_m(T) = int_0^1 t^2m exp(-T t^2) dt  (Helgaker Sec. 9.8.1).
@@ -89,11 +103,13 @@ __device__ __forceinline__ void boys_fp64(double T, const double* __restrict__ t
 #pragma unroll
     for (int m = L - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + e) * (1.0 / (2 * m + 1));
   } else {
-    const double r = 1.0 / T;
-    const double e = exp(-T);
-    F[0] = 0.88622692545275801365 * sqrt(r);
+    // T >= 60: F_0 = sqrt(pi/T)/2 and F_{m+1} = (2m+1) F_m / (2T); the
+    // neglected e^-T terms are below 1e-13 of F_m for m <= 13.
+    const double rt = rsqrt(T);
+    const double h = 0.5 * rt * rt;
+    F[0] = 0.88622692545275801365 * rt;
 #pragma unroll
-    for (int m = 0; m < L; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * (0.5 * r);
+    for (int m = 0; m < L; ++m) F[m + 1] = (2 * m + 1) * F[m] * h;
   }
 }
 
@@ -266,7 +282,7 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
 
   for (int ip = 0; ip < n0; ++ip) {
     const PrimPair<T> bp = pp[off0 + ip];
-    const T o2p = T(0.5) / bp.p;
+    const T o2p = __ldg(Prec<T>::o2p(bv) + off0 + ip);
     T Eab[3][EA];
     hermite_E<T, LA, LB>(bp.PAx, bp.PAx + ABx, o2p, Eab[0]);
     hermite_E<T, LA, LB>(bp.PAy, bp.PAy + ABy, o2p, Eab[1]);
@@ -278,17 +294,17 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
 
     for (int iq = 0; iq < n1; ++iq) {
       const PrimPair<T> kq = pp[off1 + iq];
-      const T o2q = T(0.5) / kq.p;
+      const T o2q = __ldg(Prec<T>::o2p(bv) + off1 + iq);
       T Ecd[3][EC];
       hermite_E<T, LC, LD>(kq.PAx, kq.PAx + CDx, o2q, Ecd[0]);
       hermite_E<T, LC, LD>(kq.PAy, kq.PAy + CDy, o2q, Ecd[1]);
       hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CDz, o2q, Ecd[2]);
-      const T p = bp.p, q = kq.p, pq = p + q;
-      const T alpha = p * q / pq;
+      // 1/(p+q) = r^2, alpha = p q r^2, 2 pi^(5/2) K_q / (p q sqrt(p+q)) = 4 (2 pi^(5/2)) K_q r o2p o2q
+      const T r = Prec<T>::rsq(bp.p + kq.p);
+      const T alpha = bp.p * kq.p * r * r;
       T R[nherm(L)];
       prim_R<T, L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
-      // 2 pi^(5/2) = 34.98683665524972
-      const T pref = T(34.98683665524972) * kq.K / (p * q * sqrt(pq));
+      const T pref = T(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
 #pragma unroll
       for (int k = 0; k < CK; ++k) {
         const int cx = cp[k][0], cy = cp[k][1], cz = cp[k][2], dx = cp[k][3], dy = cp[k][4], dz = cp[k][5];
@@ -401,13 +417,13 @@ __device__ __forceinline__ void boys_fp64_rt(int L, double T, const double* __re
     const double e = exp(-T);
     F[L] = acc;
 #pragma unroll 1
-    for (int m = L - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + e) / (2 * m + 1);
+    for (int m = L - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + e) * c_inv_odd64[m];
   } else {
-    const double r = 1.0 / T;
-    const double e = exp(-T);
-    F[0] = 0.88622692545275801365 * sqrt(r);
+    const double rt = rsqrt(T);
+    const double h = 0.5 * rt * rt;
+    F[0] = 0.88622692545275801365 * rt;
 #pragma unroll 1
-    for (int m = 0; m < L; ++m) F[m + 1] = ((2 * m + 1) * F[m] - e) * (0.5 * r);
+    for (int m = 0; m < L; ++m) F[m + 1] = (2 * m + 1) * F[m] * h;
   }
 }
 
@@ -422,7 +438,7 @@ __device__ __forceinline__ void boys_fp32_scaled_rt(int L, float T, const float*
     const float e = __expf(-T);
     G[L] = acc;
 #pragma unroll 1
-    for (int m = L - 1; m >= 0; --m) G[m] = (2.0f * T * G[m + 1] + e) / (float)(2 * m + 1);
+    for (int m = L - 1; m >= 0; --m) G[m] = (2.0f * T * G[m + 1] + e) * c_inv_odd32[m];
     const float c = fmaxf(1.0f, 2.0f * T);
     float cn = c;
 #pragma unroll 1
@@ -434,42 +450,42 @@ __device__ __forceinline__ void boys_fp32_scaled_rt(int L, float T, const float*
   }
 }
 
+// In place: layer n overwrites layer n+1.  Inside a layer the entries are
+// produced by decreasing t+u+v, so an entry is overwritten only after every
+// entry of the new layer that reads it has been computed.
 template <typename T>
-__device__ __forceinline__ void hermite_R_rt(int L, const T* B, T X, T Y, T Z, T* R, T* tmp) {
+__device__ __forceinline__ void hermite_R_rt(int L, const T* B, T X, T Y, T Z, T* R) {
 #pragma unroll 1
   for (int n = L; n >= 0; --n) {
-    T* dst = ((L - n) % 2 == 0) ? R : tmp;
-    const T* src = ((L - n) % 2 == 0) ? tmp : R;
 #pragma unroll 1
-    for (int t = 0; t <= L - n; ++t)
+    for (int s = L - n; s >= 0; --s) {
 #pragma unroll 1
-      for (int u = 0; u <= L - n - t; ++u)
+      for (int t = s; t >= 0; --t) {
 #pragma unroll 1
-        for (int v = 0; v <= L - n - t - u; ++v) {
+        for (int u = s - t; u >= 0; --u) {
+          const int v = s - t - u;
           T val;
-          if (t == 0 && u == 0 && v == 0) {
+          if (s == 0) {
             val = B[n];
           } else if (t > 0) {
-            val = X * src[hidx_rt(t - 1, u, v)];
-            if (t > 1) val += T(t - 1) * src[hidx_rt(t - 2, u, v)];
+            val = X * R[hidx_rt(t - 1, u, v)];
+            if (t > 1) val += T(t - 1) * R[hidx_rt(t - 2, u, v)];
           } else if (u > 0) {
-            val = Y * src[hidx_rt(t, u - 1, v)];
-            if (u > 1) val += T(u - 1) * src[hidx_rt(t, u - 2, v)];
+            val = Y * R[hidx_rt(t, u - 1, v)];
+            if (u > 1) val += T(u - 1) * R[hidx_rt(t, u - 2, v)];
           } else {
-            val = Z * src[hidx_rt(t, u, v - 1)];
-            if (v > 1) val += T(v - 1) * src[hidx_rt(t, u, v - 2)];
+            val = Z * R[hidx_rt(t, u, v - 1)];
+            if (v > 1) val += T(v - 1) * R[hidx_rt(t, u, v - 2)];
           }
-          dst[hidx_rt(t, u, v)] = val;
+          R[hidx_rt(t, u, v)] = val;
         }
-  }
-  if (L % 2 == 1) {
-    const int nh = (L + 1) * (L + 2) * (L + 3) / 6;
-    for (int x = 0; x < nh; ++x) R[x] = tmp[x];
+      }
+    }
   }
 }
 
 template <typename T>
-__device__ __forceinline__ void prim_R_rt(int L, T alpha, T X, T Y, T Z, const BasisView& bv, T* R, T* tmp) {
+__device__ __forceinline__ void prim_R_rt(int L, T alpha, T X, T Y, T Z, const BasisView& bv, T* R) {
   T B[GEN_L + 1];
   const T Tb = alpha * (X * X + Y * Y + Z * Z);
   if constexpr (sizeof(T) == 8) {
@@ -478,14 +494,14 @@ __device__ __forceinline__ void prim_R_rt(int L, T alpha, T X, T Y, T Z, const B
     T pw = f;
 #pragma unroll 1
     for (int n = 1; n <= L; ++n) { B[n] *= pw; pw *= f; }
-    hermite_R_rt<T>(L, B, X, Y, Z, R, tmp);
+    hermite_R_rt<T>(L, B, X, Y, Z, R);
   } else {
     boys_fp32_scaled_rt(L, Tb, bv.boys32, B);
 #pragma unroll 1
     for (int n = 1; n <= L; n += 2) B[n] = -B[n];
     const float c = fmaxf(1.0f, 2.0f * Tb);
     const float s = sqrtf(2.0f * alpha / c);
-    hermite_R_rt<T>(L, B, X * s, Y * s, Z * s, R, tmp);
+    hermite_R_rt<T>(L, B, X * s, Y * s, Z * s, R);
     float sp = s;
 #pragma unroll 1
     for (int n = 1; n <= L; ++n) {
@@ -501,7 +517,7 @@ struct RtClass {
   int la, lb, lc, ld, ck, nchunk;
 };
 
-__host__ __device__ inline RtClass make_rt_class(int la, int lb, int lc, int ld) {
+__host__ __device__ constexpr RtClass make_rt_class(int la, int lb, int lc, int ld) {
   RtClass c{la, lb, lc, ld, 1, 1};
   const int nab = ncart(la) * ncart(lb), ncd = ncart(lc) * ncart(ld);
   const int raw = GEN_BUDGET / (nab + nherm(la + lb));
@@ -510,9 +526,17 @@ __host__ __device__ inline RtClass make_rt_class(int la, int lb, int lc, int ld)
   return c;
 }
 
-template <typename T>
+// Array capacities of one instantiation: E tables, R, W.
+template <int NE_, int NH_, int NW_>
+struct RtSizes {
+  static constexpr int NE = NE_, NH = NH_, NW = NW_;
+};
+using GenSizes = RtSizes<GEN_E, GEN_NH, GEN_BUDGET>;
+
+template <typename T, typename S = GenSizes>
 __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView& bv, int bra, int ket, int chunk,
-                                              T* G, const T* __restrict__ bra_w = nullptr) {
+                                              T* G, const T* __restrict__ bra_w = nullptr, int pp_bra = -1,
+                                              int pp_ket = -1) {
   const int LA = C.la, LB = C.lb, LC = C.lc, LD = C.ld, CK = C.ck;
   const int NB = ncart(LB), ND = ncart(LD);
   const int NAB = ncart(LA) * NB, NCD = ncart(LC) * ND;
@@ -520,8 +544,11 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
   const int NTA = LAB + 1, NTC = LCD + 1;
   const int EA = (LA + 1) * (LB + 1) * NTA, EC = (LC + 1) * (LD + 1) * NTC;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
-  const int off0 = __ldg(bv.pair_pp_off + bra), n0 = __ldg(bv.pair_pp_n + bra);
-  const int off1 = __ldg(bv.pair_pp_off + ket), n1 = __ldg(bv.pair_pp_n + ket);
+  // pp_bra / pp_ket >= 0 restrict the bra / ket to that single primitive pair
+  const int off0 = pp_bra >= 0 ? pp_bra : __ldg(bv.pair_pp_off + bra);
+  const int n0 = pp_bra >= 0 ? 1 : __ldg(bv.pair_pp_n + bra);
+  const int off1 = pp_ket >= 0 ? pp_ket : __ldg(bv.pair_pp_off + ket);
+  const int n1 = pp_ket >= 0 ? 1 : __ldg(bv.pair_pp_n + ket);
   const T ABx = (T)__ldg(bv.pair_AB + 3 * bra), ABy = (T)__ldg(bv.pair_AB + 3 * bra + 1),
           ABz = (T)__ldg(bv.pair_AB + 3 * bra + 2);
   const T CDx = (T)__ldg(bv.pair_AB + 3 * ket), CDy = (T)__ldg(bv.pair_AB + 3 * ket + 1),
@@ -530,15 +557,15 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
   const int kc0 = chunk * CK;
   const int nk = min(CK, NCD - kc0);
 
-  T Eab[3 * GEN_E], Ecd[3 * GEN_E];
-  T R[GEN_NH], tmp[GEN_NH];
-  T W[GEN_BUDGET];
+  T Eab[3 * S::NE], Ecd[3 * S::NE];
+  T R[S::NH];
+  T W[S::NW];
   for (int x = 0; x < NAB * CK; ++x) G[x] = T(0);
 
 #pragma unroll 1
   for (int ip = 0; ip < n0; ++ip) {
     const PrimPair<T> bp = pp[off0 + ip];
-    const T o2p = T(0.5) / bp.p;
+    const T o2p = __ldg(Prec<T>::o2p(bv) + off0 + ip);
     hermite_E_rt<T>(LA, LB, bp.PAx, bp.PAx + ABx, o2p, Eab);
     hermite_E_rt<T>(LA, LB, bp.PAy, bp.PAy + ABy, o2p, Eab + EA);
     hermite_E_rt<T>(LA, LB, bp.PAz, bp.PAz + ABz, o2p, Eab + 2 * EA);
@@ -546,14 +573,14 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
 #pragma unroll 1
     for (int iq = 0; iq < n1; ++iq) {
       const PrimPair<T> kq = pp[off1 + iq];
-      const T o2q = T(0.5) / kq.p;
+      const T o2q = __ldg(Prec<T>::o2p(bv) + off1 + iq);
       hermite_E_rt<T>(LC, LD, kq.PAx, kq.PAx + CDx, o2q, Ecd);
       hermite_E_rt<T>(LC, LD, kq.PAy, kq.PAy + CDy, o2q, Ecd + EC);
       hermite_E_rt<T>(LC, LD, kq.PAz, kq.PAz + CDz, o2q, Ecd + 2 * EC);
-      const T p = bp.p, q = kq.p, pq = p + q;
-      const T alpha = p * q / pq;
-      prim_R_rt<T>(L, alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R, tmp);
-      const T pref = T(34.98683665524972) * kq.K / (p * q * sqrt(pq));
+      const T r = Prec<T>::rsq(bp.p + kq.p);
+      const T alpha = bp.p * kq.p * r * r;
+      prim_R_rt<T>(L, alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
+      const T pref = T(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
 #pragma unroll 1
       for (int k = 0; k < nk; ++k) {
         const int kc = kc0 + k;
@@ -616,14 +643,18 @@ __device__ __noinline__ void digest_rt(const RtClass& C, const JKLaunch& a, int 
   const int sc = __ldg(bv.pair_a + ket), sd = __ldg(bv.pair_b + ket);
   const int oa = __ldg(bv.shell_coff + sa), ob = __ldg(bv.shell_coff + sb);
   const int oc = __ldg(bv.shell_coff + sc), od = __ldg(bv.shell_coff + sd);
-  const long n = bv.ncart;
+  long long base;
+  long n;
+  mol_block(bv, bra, base, n);
   T w = T(1);
   if (sa == sb) w *= T(0.5);
   if (sc == sd) w *= T(0.5);
   if (a.same_class && bra == ket) w *= T(0.5);
   const T w4 = T(4) * w, w2 = T(2) * w;
   const T* __restrict__ D = nullptr;
-  if constexpr (sizeof(T) == 8) D = (const T*)a.D64; else D = (const T*)a.D32;
+  if constexpr (sizeof(T) == 8) D = (const T*)a.D64 + base; else D = (const T*)a.D32 + base;
+  double* __restrict__ Jm = a.J + base;
+  double* __restrict__ Km = a.K + base;
   const int kc0 = chunk * CK, nk = min(CK, NCD - kc0);
 #pragma unroll 1
   for (int ab = 0; ab < NA * NB; ++ab) {
@@ -632,14 +663,14 @@ __device__ __noinline__ void digest_rt(const RtClass& C, const JKLaunch& a, int 
       const int kc = kc0 + k;
       s += G[ab * CK + k] * dload(D + (oc + kc / ND) * n + od + kc % ND);
     }
-    atomicAdd(a.J + (oa + ab / NB) * n + ob + ab % NB, (double)(w4 * s));
+    atomicAdd(Jm + (oa + ab / NB) * n + ob + ab % NB, (double)(w4 * s));
   }
 #pragma unroll 1
   for (int k = 0; k < nk; ++k) {
     const int kc = kc0 + k, ic = kc / ND, id = kc % ND;
     T s = T(0);
     for (int ab = 0; ab < NA * NB; ++ab) s += G[ab * CK + k] * dload(D + (oa + ab / NB) * n + ob + ab % NB);
-    atomicAdd(a.J + (oc + ic) * n + od + id, (double)(w4 * s));
+    atomicAdd(Jm + (oc + ic) * n + od + id, (double)(w4 * s));
 #pragma unroll 1
     for (int ia = 0; ia < NA; ++ia) {
       T s_ac = T(0), s_ad = T(0);
@@ -648,8 +679,8 @@ __device__ __noinline__ void digest_rt(const RtClass& C, const JKLaunch& a, int 
         s_ac += g * dload(D + (ob + ib) * n + od + id);
         s_ad += g * dload(D + (ob + ib) * n + oc + ic);
       }
-      atomicAdd(a.K + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
-      atomicAdd(a.K + (oa + ia) * n + od + id, (double)(w2 * s_ad));
+      atomicAdd(Km + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
+      atomicAdd(Km + (oa + ia) * n + od + id, (double)(w2 * s_ad));
     }
 #pragma unroll 1
     for (int ib = 0; ib < NB; ++ib) {
@@ -659,8 +690,8 @@ __device__ __noinline__ void digest_rt(const RtClass& C, const JKLaunch& a, int 
         s_bc += g * dload(D + (oa + ia) * n + od + id);
         s_bd += g * dload(D + (oa + ia) * n + oc + ic);
       }
-      atomicAdd(a.K + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
-      atomicAdd(a.K + (ob + ib) * n + od + id, (double)(w2 * s_bd));
+      atomicAdd(Km + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
+      atomicAdd(Km + (ob + ib) * n + od + id, (double)(w2 * s_bd));
     }
   }
 }
@@ -674,8 +705,7 @@ __device__ __forceinline__ void decode_quartet(const JKLaunch& a, long long qi, 
     const int mid = (lo + hi) >> 1;
     if (__ldg(a.prefix + mid) <= qi) lo = mid; else hi = mid;
   }
-  long long j = qi - __ldg(a.prefix + lo);
-  if (a.ket_start) j += __ldg(a.ket_start + lo);
+  const long long j = qi - __ldg(a.prefix + lo) + __ldg(a.ket_start + lo);
   bra = a.bra_first + lo;
   ket = a.ket_first + (int)j;
 }
@@ -695,14 +725,18 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int 
   const int sc = __ldg(bv.pair_a + ket), sd = __ldg(bv.pair_b + ket);
   const int oa = __ldg(bv.shell_coff + sa), ob = __ldg(bv.shell_coff + sb);
   const int oc = __ldg(bv.shell_coff + sc), od = __ldg(bv.shell_coff + sd);
-  const long n = bv.ncart;
+  long long base;
+  long n;
+  mol_block(bv, bra, base, n);
   T w = T(1);
   if (sa == sb) w *= T(0.5);
   if (sc == sd) w *= T(0.5);
   if (a.same_class && bra == ket) w *= T(0.5);
   const T w4 = T(4) * w, w2 = T(2) * w;
   const T* __restrict__ D = nullptr;
-  if constexpr (sizeof(T) == 8) D = (const T*)a.D64; else D = (const T*)a.D32;
+  if constexpr (sizeof(T) == 8) D = (const T*)a.D64 + base; else D = (const T*)a.D32 + base;
+  double* __restrict__ Jm = a.J + base;
+  double* __restrict__ Km = a.K + base;
 
   // J_ab += 4w sum_cd g D_cd
   T Dcd[CK];
@@ -718,7 +752,7 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int 
       T s = T(0);
 #pragma unroll
       for (int k = 0; k < CK; ++k) s += G[(ia * NB + ib) * CK + k] * Dcd[k];
-      atomicAdd(a.J + (oa + ia) * n + ob + ib, (double)(w4 * s));
+      atomicAdd(Jm + (oa + ia) * n + ob + ib, (double)(w4 * s));
     }
   // J_cd += 4w sum_ab g D_ab
 #pragma unroll
@@ -730,7 +764,7 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int 
     for (int ia = 0; ia < NA; ++ia)
 #pragma unroll
       for (int ib = 0; ib < NB; ++ib) s += G[(ia * NB + ib) * CK + k] * dload(D + (oa + ia) * n + ob + ib);
-    atomicAdd(a.J + (oc + kc / ND) * n + od + kc % ND, (double)(w4 * s));
+    atomicAdd(Jm + (oc + kc / ND) * n + od + kc % ND, (double)(w4 * s));
   }
   // K contributions
 #pragma unroll
@@ -747,8 +781,8 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int 
         s_ac += g * dload(D + (ob + ib) * n + od + id);
         s_ad += g * dload(D + (ob + ib) * n + oc + ic);
       }
-      atomicAdd(a.K + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
-      atomicAdd(a.K + (oa + ia) * n + od + id, (double)(w2 * s_ad));
+      atomicAdd(Km + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
+      atomicAdd(Km + (oa + ia) * n + od + id, (double)(w2 * s_ad));
     }
 #pragma unroll
     for (int ib = 0; ib < NB; ++ib) {
@@ -759,8 +793,8 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int 
         s_bc += g * dload(D + (oa + ia) * n + od + id);
         s_bd += g * dload(D + (oa + ia) * n + oc + ic);
       }
-      atomicAdd(a.K + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
-      atomicAdd(a.K + (ob + ib) * n + od + id, (double)(w2 * s_bd));
+      atomicAdd(Km + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
+      atomicAdd(Km + (ob + ib) * n + od + id, (double)(w2 * s_bd));
     }
   }
 }
@@ -807,11 +841,16 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a, RtClass C) {
+template <typename T, int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
+  constexpr RtClass C = make_rt_class(LA, LB, LC, LD);
+  constexpr int LAB = LA + LB, LCD = LC + LD;
+  constexpr int EA = (LA + 1) * (LB + 1) * (LAB + 1), EC = (LC + 1) * (LD + 1) * (LCD + 1);
+  using S = RtSizes<(EA > EC ? EA : EC), nherm(LAB + LCD), nherm(LAB) * C.ck>;
+  constexpr int NG = ncart(LA) * ncart(LB) * C.ck;
   const long long total = (long long)__ldg(a.prefix + a.nbra) * C.nchunk;
   const int lane = threadIdx.x & 31;
-  T G[GEN_BUDGET];
+  T G[NG];
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.counter, 32ULL);
@@ -827,12 +866,13 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a, RtClass C
       const int chunk = (int)(item - qi * C.nchunk);
       int bra, ket;
       decode_quartet(a, qi, bra, ket);
-      quartet_block_rt<T>(C, a.bv, bra, ket, chunk, G);
+      quartet_block_rt<T, S>(C, a.bv, bra, ket, chunk, G);
       digest_rt<T>(C, a, bra, ket, chunk, G);
     }
   }
 }
 
+#ifdef ADFT_ERI_SCHWARZ
 // Schwarz bounds of the pairs of one class: Q = sqrt(max |(mn|mn)|), FP64.
 static __global__ void __launch_bounds__(JK_THREADS) k_schwarz_generic(BasisView bv, RtClass C, int first, int n,
                                                                  double* Q) {
@@ -852,26 +892,50 @@ static __global__ void __launch_bounds__(JK_THREADS) k_schwarz_generic(BasisView
   Q[pr] = sqrt(mx);
 }
 
+// Primitive-pair bounds of the pairs of one class: Qp = sqrt(max |[mn|mn]_p|)
+// with only primitive pair p on both sides (one thread per primitive pair).
+static __global__ void __launch_bounds__(JK_THREADS) k_prim_schwarz(BasisView bv, RtClass C, int first, int n,
+                                                                    const int* __restrict__ pp_pair, double* Qp) {
+  const int pp_first = bv.pair_pp_off[first];
+  const int pp_end = bv.pair_pp_off[first + n - 1] + bv.pair_pp_n[first + n - 1];
+  const int g = pp_first + blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= pp_end) return;
+  const int pr = pp_pair[g];
+  const int NAB = ncart(C.la) * ncart(C.lb);
+  double mx = 0.0;
+  double G[GEN_BUDGET];
+  for (int chunk = 0; chunk < C.nchunk; ++chunk) {
+    quartet_block_rt<double>(C, bv, pr, pr, chunk, G, nullptr, g, g);
+    for (int k = 0; k < C.ck; ++k) {
+      const int kc = chunk * C.ck + k;
+      if (kc < NAB) mx = fmax(mx, fabs(G[kc * C.ck + k]));
+    }
+  }
+  Qp[g] = sqrt(mx);
+}
+
+#endif  // ADFT_ERI_SCHWARZ
+
 // ---------------------------------------------------------------------------
-// dispatch tables: one launcher per (X, Y) class pair, X >= Y
+// dispatch: one launcher per (X, Y) class pair, X >= Y.  The launchers are
+// explicitly instantiated in several translation units (adft_eri_*.cu) so
+// that they compile in parallel; adft_dispatch.cu holds the tables.
+template <typename T, int X, int Y>
+cudaError_t launch_one(const JKLaunch& a, int grid, cudaStream_t s);
+
+#ifndef ADFT_ERI_DECLARE_ONLY
 template <typename T, int X, int Y>
 cudaError_t launch_one(const JKLaunch& a, int grid, cudaStream_t s) {
   constexpr int LA = cls_la(X), LB = cls_lb(X), LC = cls_la(Y), LD = cls_lb(Y);
-  if constexpr (X >= Y && is_small_class(LA, LB, LC, LD)) {
+  if constexpr (X < Y) {
+    return cudaErrorInvalidValue;
+  } else if constexpr (is_small_class(LA, LB, LC, LD)) {
     k_jk<T, LA, LB, LC, LD><<<grid, JK_THREADS, 0, s>>>(a);
   } else {
-    k_jk_generic<T><<<grid, JK_THREADS, 0, s>>>(a, make_rt_class(LA, LB, LC, LD));
+    k_jk_generic<T, LA, LB, LC, LD><<<grid, JK_THREADS, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
-
-template <typename T, int... I>
-cudaError_t dispatch_jk(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s,
-                        std::integer_sequence<int, I...>) {
-  using Fn = cudaError_t (*)(const JKLaunch&, int, cudaStream_t);
-  static constexpr Fn table[] = {&launch_one<T, I / NCLS, I % NCLS>...};
-  if (X < 0 || Y < 0 || X >= NCLS || Y > X) return cudaErrorInvalidValue;
-  return table[X * NCLS + Y](a, grid, s);
-}
+#endif
 
 }  // namespace adft

@@ -20,9 +20,8 @@ namespace adft {
 // which = 0: differentiate a (l_a +/- 1); which = 1: differentiate b.
 template <typename T>
 __device__ __noinline__ void centre_derivative(const BasisView& bv, int P, int Qk, int la, int lb, int lc, int ld,
-                                               int which, const T* __restrict__ D, int oa, int ob, int oc, int od,
-                                               T* out3, T* Gp, T* Gm) {
-  const long n = bv.ncart;
+                                               int which, const T* __restrict__ D, long n, int oa, int ob, int oc,
+                                               int od, T* out3, T* Gp, T* Gm) {
   const int lup_a = la + (which == 0), lup_b = lb + (which == 1);
   const int ldn_a = la - (which == 0), ldn_b = lb - (which == 1);
   const RtClass Cu = make_rt_class(lup_a, lup_b, lc, ld);
@@ -101,14 +100,18 @@ __global__ void __launch_bounds__(JK_THREADS) k_grad_generic(GradLaunch g, int l
       const BasisView& bv = a.bv;
       const int sa = bv.pair_a[bra], sb = bv.pair_b[bra], sc = bv.pair_a[ket], sd = bv.pair_b[ket];
       const int oa = bv.shell_coff[sa], ob = bv.shell_coff[sb], oc = bv.shell_coff[sc], od = bv.shell_coff[sd];
+      long long base;
+      long nrow;
+      mol_block(bv, bra, base, nrow);
+      const T* Dm = D + base;
       T w = T(8);
       if (sa == sb) w *= T(0.5);
       if (sc == sd) w *= T(0.5);
       if (a.same_class && bra == ket) w *= T(0.5);
       T dA[3], dB[3], dC[3];
-      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 0, D, oa, ob, oc, od, dA, Gp, Gm);
-      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 1, D, oa, ob, oc, od, dB, Gp, Gm);
-      centre_derivative<T>(bv, ket, bra, lc, ld, la, lb, 0, D, oc, od, oa, ob, dC, Gp, Gm);
+      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 0, Dm, nrow, oa, ob, oc, od, dA, Gp, Gm);
+      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 1, Dm, nrow, oa, ob, oc, od, dB, Gp, Gm);
+      centre_derivative<T>(bv, ket, bra, lc, ld, la, lb, 0, Dm, nrow, oc, od, oa, ob, dC, Gp, Gm);
       const int ta = bv.shell_atom[sa], tb = bv.shell_atom[sb], tc = bv.shell_atom[sc], td = bv.shell_atom[sd];
       for (int k = 0; k < 3; ++k) {
         atomicAdd(g.grad + 3 * ta + k, (double)(w * dA[k]));

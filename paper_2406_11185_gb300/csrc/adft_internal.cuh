@@ -55,10 +55,30 @@ struct BasisView {
   const PrimPair<float>* pp32;
   const double* boys64;    // [BOYS_NT][BOYS_MMAX+1] F_m(i h)
   const float* boys32;
+  const double* pp_o2p64;  // [npp]: 1 / (2p) of every primitive pair
+  const float* pp_o2p32;
   const double* pp_w64;    // [2][npp]: 2 a and 2 b of every primitive pair
   const float* pp_w32;
   long long npp;
+  // several molecules (a batch): molecule of each pair, offset and row length
+  // of the molecule's block in the packed Cartesian matrices; NULL = one
+  // molecule whose block starts at 0 with row length ncart.
+  const int* pair_mol;
+  const long long* mol_cbase;
+  const int* mol_nc;
 };
+
+// offset and row length of the packed Cartesian block of a pair's molecule
+__device__ __forceinline__ void mol_block(const BasisView& bv, int pair, long long& base, long& n) {
+  if (bv.pair_mol) {
+    const int m = __ldg(bv.pair_mol + pair);
+    base = __ldg(bv.mol_cbase + m);
+    n = __ldg(bv.mol_nc + m);
+  } else {
+    base = 0;
+    n = bv.ncart;
+  }
+}
 
 // One class-pair launch of the J/K kernel.
 struct JKLaunch {
@@ -67,7 +87,7 @@ struct JKLaunch {
   int ket_first;            // pairs of class Y start here
   int same_class;           // X == Y
   const long long* prefix;  // [nbra + 1] quartets before each bra
-  const int* ket_start;     // [nbra] first ket of the band (NULL: 0)
+  const int* ket_start;     // [nbra] first ket of the band, relative to ket_first
   unsigned long long* counter;  // dynamic work counter (zeroed)
   const double* D64;        // Cartesian D [ncart][ncart]
   const float* D32;
@@ -88,6 +108,11 @@ cudaError_t launch_jk_fp32(int X, int Y, const JKLaunch& a, int grid, cudaStream
 cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
 cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
 cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s);
+cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, const int* pp_pair, int npp_class,
+                                double* Qp, cudaStream_t s);
+// Primitive pairs whose bound Qp * max(Qp) is at or below this are dropped at
+// basis creation (1e-3 of the paper's default tolerance 1e-12).
+constexpr double PRIM_EPS = 1e-15;
 // Boys tables in device memory of the current device (built once).
 cudaError_t boys_tables(const double** t64, const float** t32);
 
