@@ -231,6 +231,28 @@ int adft_batch_autotune(adft_batch* bt, const double* D_packed, const adft_opts*
 
 void adft_batch_destroy(adft_batch* bt);
 
+/* ---- energy without allocation ------------------------------------------ */
+
+/* Largest nbf accepted by adft_energy_static: the size, in doubles, of the
+ * library's built-in device scratch array (128 KiB on every device that
+ * loads the library, held until the process exits). */
+#define ADFT_STATIC_MAX_NBF 16384
+
+/* E = 1/2 tr(DJ) - 1/4 tr(DK) from caller-owned D, J, K, for callers that
+ * cannot allocate device memory at the point of the call (a memory pool that
+ * forbids growth, a region where cudaMalloc would synchronise the device, an
+ * allocator owned by another framework).  The paper has no counterpart; it is
+ * a convenience of this library.  It allocates nothing: its scratch (one
+ * partial sum per row) is a fixed array inside the library, so every call
+ * shares it and keeps the last call's contents, and calls that overlap on the
+ * GPU race on it (serialise them, e.g. on one stream).
+ *   D, J, K: dev [nbf*nbf] row-major float64.  E: dev pointer to one float64.
+ *   nbf: 1..ADFT_STATIC_MAX_NBF, else ADFT_ERR_ARG.  stream: cudaStream_t or
+ *   NULL.  Asynchronous.  The first call on each device looks up the device
+ *   address of the scratch array (with that device current); make that first
+ *   call before any stream capture. */
+int adft_energy_static(const double* D, const double* J, const double* K, int nbf, double* E, void* stream);
+
 /* ---- utilities ---------------------------------------------------------- */
 
 const char* adft_status_string(int status);

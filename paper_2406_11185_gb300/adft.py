@@ -27,13 +27,14 @@ ADFT_PREC_FP64 = 0
 ADFT_PREC_MIXED = 1
 ADFT_LMAX = 3
 ADFT_MAX_NPRIM = 16
+ADFT_STATIC_MAX_NBF = 16384
 
 EXPORTED = [
     "adft_basis_create", "adft_basis_nbf", "adft_basis_dims", "adft_basis_schwarz", "adft_jk_build",
     "adft_jk_energy", "adft_jk_grad", "adft_jk_last_stats", "adft_jk_last_timings", "adft_basis_set_abort", "adft_jk_status",
     "adft_basis_destroy", "adft_batch_create", "adft_batch_offsets", "adft_batch_grad_offsets", "adft_batch_jk",
     "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version", "adft_autotune",
-    "adft_set_tuning", "adft_jk_plan", "adft_batch_last_stats", "adft_batch_last_timings", "adft_batch_autotune",
+    "adft_set_tuning", "adft_jk_plan", "adft_energy_static", "adft_batch_last_stats", "adft_batch_last_timings", "adft_batch_autotune",
 ]
 
 
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH):
     L.adft_batch_last_stats.argtypes = [vp, ctypes.POINTER(adft_stats)]
     L.adft_batch_last_timings.argtypes = [vp, dp]
     L.adft_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(adft_opts), ctypes.POINTER(ctypes.c_int), dp]
+    L.adft_energy_static.argtypes = [vp, vp, vp, ip, vp, vp]
     L.adft_status_string.argtypes = [ip]
     L.adft_status_string.restype = ctypes.c_char_p
     L.adft_last_error_message.restype = ctypes.c_char_p
@@ -365,3 +367,18 @@ def adft_batch_autotune(batch: Batch, D_packed, thresh=1e-10, split=1e-5, precis
     _check(load().adft_batch_autotune(batch.handle, ctypes.c_void_p(D_packed.data_ptr()), ctypes.byref(o), tab,
                                       None), "adft_batch_autotune")
     return np.array(tab[:], dtype=np.int32).reshape(2, NCP)
+
+
+def adft_energy_static(D, J, K, stream=None):
+    """E = 1/2 tr(DJ) - 1/4 tr(DK) with no device allocation inside the call
+    (scratch is a fixed array in the library); returns a 1-element CUDA
+    tensor.  The output tensor is allocated here by PyTorch, before the call."""
+    import torch
+    n = D.shape[0]
+    for M in (D, J, K):
+        _check_matrix(M, n)
+    E = torch.empty(1, dtype=torch.float64, device=D.device)
+    vp = ctypes.c_void_p
+    _check(load().adft_energy_static(vp(D.data_ptr()), vp(J.data_ptr()), vp(K.data_ptr()), n, vp(E.data_ptr()),
+                                     _stream_ptr(stream)), "adft_energy_static")
+    return E
