@@ -163,7 +163,7 @@ int adft_jk_last_stats(adft_basis* b, adft_stats* st);
 int adft_jk_last_timings(adft_basis* b, double* ms);
 
 /* Autotuner (per angular-momentum class pair and precision band): times
- * every class-pair kernel of one build of D with 1, 2, 4, 8 and 16 resident
+ * every class-pair kernel of one build of D with 1, 2, 4 and 8 resident
  * blocks per SM and keeps the fastest launch shape in the handle for later
  * calls.  The J/K accumulators of the handle are left undefined.
  *   table: host [2][55] ints (band-major: FP64 then FP32; class pair

@@ -1,0 +1,300 @@
+// Group-cooperative J/K kernel for the larger angular-momentum classes.
+//
+// A group of GS lanes (GS = number of ket Cartesian components, at most 32)
+// owns one shell quartet.  Lane gl owns ket components gl, gl+GS, ...; for
+// every bra primitive p the group evaluates the Hermite integrals R of up to
+// SLOTS ket primitives at once (one ket primitive per lane, written to shared
+// memory together with that primitive's ket Hermite expansion coefficients),
+// then every lane applies the ket transform of its own components to all of
+// them:  W_p[tuv][cd] += sum_{tau nu phi} (+-) E^cd_{tau nu phi} R_{t+tau,u+nu,v+phi}.
+// The bra transform of W_p is accumulated into the contracted block in
+// shared memory, and the J/K digestion reads that block.  Compared with one
+// thread per quartet this computes R once per primitive quartet instead of
+// once per component chunk, and keeps every array out of local memory.
+#pragma once
+// (included by adft_eri.cuh inside namespace adft)
+
+constexpr int COOP_SLOT_CAP = 8;
+constexpr int COOP_SMEM_BUDGET = 200 * 1024;
+constexpr int COOP_MAX_WARPS = 8;
+
+// In place Hermite integrals with compile-time L (same ordering argument as
+// hermite_R_rt: layer n overwrites layer n+1 by decreasing t+u+v).
+template <typename T, int L>
+__device__ __forceinline__ void hermite_R_inplace(const T* B, T X, T Y, T Z, T* R) {
+#pragma unroll
+  for (int n = L; n >= 0; --n)
+#pragma unroll
+    for (int s = L - n; s >= 0; --s)
+#pragma unroll
+      for (int t = s; t >= 0; --t)
+#pragma unroll
+        for (int u = s - t; u >= 0; --u) {
+          const int v = s - t - u;
+          T val;
+          if (s == 0) {
+            val = B[n];
+          } else if (t > 0) {
+            val = X * R[hidx(t - 1, u, v)];
+            if (t > 1) val += T(t - 1) * R[hidx(t - 2, u, v)];
+          } else if (u > 0) {
+            val = Y * R[hidx(t, u - 1, v)];
+            if (u > 1) val += T(u - 1) * R[hidx(t, u - 2, v)];
+          } else {
+            val = Z * R[hidx(t, u, v - 1)];
+            if (v > 1) val += T(v - 1) * R[hidx(t, u, v - 2)];
+          }
+          R[hidx(t, u, v)] = val;
+        }
+}
+
+// pref * R_tuv of one primitive quartet into R (any memory space)
+template <typename T, int L>
+__device__ __forceinline__ void prim_R_scaled(T alpha, T X, T Y, T Z, T pref, const BasisView& bv, T* R) {
+  T B[L + 1];
+  const T Tb = alpha * (X * X + Y * Y + Z * Z);
+  if constexpr (sizeof(T) == 8) {
+    boys_fp64<L>(Tb, bv.boys64, B);
+    const T f = -2.0 * alpha;
+    T pw = pref;
+#pragma unroll
+    for (int n = 0; n <= L; ++n) { B[n] *= pw; pw *= f; }
+    hermite_R_inplace<T, L>(B, X, Y, Z, R);
+  } else {
+    boys_fp32_scaled<L>(Tb, bv.boys32, B);
+#pragma unroll
+    for (int n = 0; n <= L; ++n) B[n] *= (n & 1) ? -pref : pref;
+    const float c = fmaxf(1.0f, 2.0f * Tb);
+    const float s = sqrtf(2.0f * alpha / c);
+    hermite_R_inplace<T, L>(B, X * s, Y * s, Z * s, R);
+    float sp = s;
+#pragma unroll
+    for (int n = 1; n <= L; ++n) {
+#pragma unroll
+      for (int x = nherm(n - 1); x < nherm(n); ++x) R[x] *= sp;
+      sp *= s;
+    }
+  }
+}
+
+// J/K digestion from the contracted block Gs[ab][cd] in shared memory; lane
+// gl of a group of GS lanes handles ket components gl, gl+GS, ... (same
+// weights and targets as digest()).
+template <typename T, int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket, int gl, int GS, const T* Gs) {
+  constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+  constexpr int NAB = NA * NB, NCD = NC * ND;
+  const BasisView& bv = a.bv;
+  const int sa = __ldg(bv.pair_a + bra), sb = __ldg(bv.pair_b + bra);
+  const int sc = __ldg(bv.pair_a + ket), sd = __ldg(bv.pair_b + ket);
+  const int oa = __ldg(bv.shell_coff + sa), ob = __ldg(bv.shell_coff + sb);
+  const int oc = __ldg(bv.shell_coff + sc), od = __ldg(bv.shell_coff + sd);
+  long long base;
+  long n;
+  mol_block(bv, bra, base, n);
+  T w = T(1);
+  if (sa == sb) w *= T(0.5);
+  if (sc == sd) w *= T(0.5);
+  if (a.same_class && bra == ket) w *= T(0.5);
+  const T w4 = T(4) * w, w2 = T(2) * w;
+  const T* __restrict__ D = nullptr;
+  if constexpr (sizeof(T) == 8) D = (const T*)a.D64 + base; else D = (const T*)a.D32 + base;
+  double* __restrict__ Jm = a.J + base;
+  double* __restrict__ Km = a.K + base;
+  // J_ab partial over this lane's ket components
+  for (int ab = 0; ab < NAB; ++ab) {
+    T s = T(0);
+    for (int kc = gl; kc < NCD; kc += GS) s += Gs[ab * NCD + kc] * __ldg(D + (oc + kc / ND) * n + od + kc % ND);
+    atomicAdd(Jm + (oa + ab / NB) * n + ob + ab % NB, (double)(w4 * s));
+  }
+  for (int kc = gl; kc < NCD; kc += GS) {
+    const int ic = kc / ND, id = kc % ND;
+    T s = T(0);
+    for (int ab = 0; ab < NAB; ++ab) s += Gs[ab * NCD + kc] * __ldg(D + (oa + ab / NB) * n + ob + ab % NB);
+    atomicAdd(Jm + (oc + ic) * n + od + id, (double)(w4 * s));
+    for (int ia = 0; ia < NA; ++ia) {
+      T s_ac = T(0), s_ad = T(0);
+      for (int ib = 0; ib < NB; ++ib) {
+        const T g = Gs[(ia * NB + ib) * NCD + kc];
+        s_ac += g * __ldg(D + (ob + ib) * n + od + id);
+        s_ad += g * __ldg(D + (ob + ib) * n + oc + ic);
+      }
+      atomicAdd(Km + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
+      atomicAdd(Km + (oa + ia) * n + od + id, (double)(w2 * s_ad));
+    }
+    for (int ib = 0; ib < NB; ++ib) {
+      T s_bc = T(0), s_bd = T(0);
+      for (int ia = 0; ia < NA; ++ia) {
+        const T g = Gs[(ia * NB + ib) * NCD + kc];
+        s_bc += g * __ldg(D + (oa + ia) * n + od + id);
+        s_bd += g * __ldg(D + (oa + ia) * n + oc + ic);
+      }
+      atomicAdd(Km + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
+      atomicAdd(Km + (ob + ib) * n + od + id, (double)(w2 * s_bd));
+    }
+  }
+}
+
+template <typename T, int LA, int LB, int LC, int LD>
+struct CoopPlan {
+  static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+  static constexpr int NAB = NA * NB, NCD = NC * ND;
+  static constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
+  static constexpr int NHAB = nherm(LAB), NH = nherm(L);
+  static constexpr int EA = (LA + 1) * (LB + 1) * (LAB + 1), EC = (LC + 1) * (LD + 1) * (LCD + 1);
+  static constexpr int GS = NCD < 32 ? NCD : 32;
+  static constexpr int CK = (NCD + GS - 1) / GS;
+  static constexpr int NGW = 32 / GS;
+  static constexpr int SLOTS = GS < COOP_SLOT_CAP ? GS : COOP_SLOT_CAP;
+  static constexpr int SLOT = NH + 3 * EC;
+  static constexpr int GROUP = SLOTS * SLOT + NAB * NCD + 3 * EA;
+  static constexpr int WARP_BYTES = NGW * GROUP * (int)sizeof(T);
+  static constexpr int WFIT = COOP_SMEM_BUDGET / WARP_BYTES;
+  static constexpr int WARPS = WFIT > COOP_MAX_WARPS ? COOP_MAX_WARPS : WFIT;
+  static constexpr int WREG = NHAB * CK;  // W values per lane (registers)
+  // classes up to d shells (f classes keep the runtime-L kernel, which
+  // compiles far faster)
+  static constexpr bool fits = WARPS >= 1 && WREG <= (sizeof(T) == 8 ? 80 : 160) && LA <= 2 && LC <= 2;
+  static constexpr int SMEM = WARPS * WARP_BYTES;
+};
+
+template <typename T, int LA, int LB, int LC, int LD>
+__global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
+  using P = CoopPlan<T, LA, LB, LC, LD>;
+  constexpr int NB = P::NB, ND = P::ND, NAB = P::NAB, NCD = P::NCD, GS = P::GS, CK = P::CK;
+  constexpr int NHAB = P::NHAB, NH = P::NH, EA = P::EA, EC = P::EC, LAB = P::LAB;
+  constexpr int NTA = LAB + 1, NTC = P::LCD + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / GS, gl = lane - g * GS;
+  const bool in_group = g < P::NGW;
+  T* gbase = reinterpret_cast<T*>(smem_raw) + (size_t)(warp * P::NGW + (in_group ? g : 0)) * P::GROUP;
+  T* slots = gbase;                     // [SLOTS][SLOT]: R then 3 x EC ket E tables
+  T* Gs = gbase + P::SLOTS * P::SLOT;   // [NAB][NCD] contracted block
+  T* Eab = Gs + NAB * NCD;              // [3][EA] bra E of the current bra primitive
+  const unsigned gmask = (GS == 32) ? 0xffffffffu : (((1u << GS) - 1u) << (g * GS));
+  const long long total = (long long)__ldg(a.prefix + a.nbra);
+  const BasisView& bv = a.bv;
+  const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
+  const T* __restrict__ o2pa = Prec<T>::o2p(bv);
+
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)P::NGW);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((long long)base >= total) break;
+    if (*(volatile const int*)a.abort_flag) {
+      if (lane == 0) atomicCAS(a.status, 0, ADFT_ERR_ABORTED);
+      break;
+    }
+    const long long qi = (long long)base + g;
+    if (!in_group || qi >= total) continue;
+    int bra, ket;
+    decode_quartet(a, qi, bra, ket);
+    const int off0 = __ldg(bv.pair_pp_off + bra), n0 = __ldg(bv.pair_pp_n + bra);
+    const int off1 = __ldg(bv.pair_pp_off + ket), n1 = __ldg(bv.pair_pp_n + ket);
+    const T AB[3] = {(T)__ldg(bv.pair_AB + 3 * bra), (T)__ldg(bv.pair_AB + 3 * bra + 1),
+                     (T)__ldg(bv.pair_AB + 3 * bra + 2)};
+    const T CDx = (T)__ldg(bv.pair_AB + 3 * ket), CDy = (T)__ldg(bv.pair_AB + 3 * ket + 1),
+            CDz = (T)__ldg(bv.pair_AB + 3 * ket + 2);
+    for (int kc = gl; kc < NCD; kc += GS)
+      for (int ab = 0; ab < NAB; ++ab) Gs[ab * NCD + kc] = T(0);
+
+    for (int ip = 0; ip < n0; ++ip) {
+      const PrimPair<T> bp = pp[off0 + ip];
+      const T o2p = __ldg(o2pa + off0 + ip);
+      if (gl < 3) {
+        const T PA = gl == 0 ? bp.PAx : gl == 1 ? bp.PAy : bp.PAz;
+        hermite_E<T, LA, LB>(PA, PA + AB[gl], o2p, Eab + gl * EA);
+      }
+      T W[NHAB * CK];
+#pragma unroll
+      for (int x = 0; x < NHAB * CK; ++x) W[x] = T(0);
+      __syncwarp(gmask);
+      for (int q0 = 0; q0 < n1; q0 += P::SLOTS) {
+        const int nv = min(P::SLOTS, n1 - q0);
+        if (gl < nv) {
+          const int iq = off1 + q0 + gl;
+          const PrimPair<T> kq = pp[iq];
+          const T o2q = __ldg(o2pa + iq);
+          T* sl = slots + gl * P::SLOT;
+          hermite_E<T, LC, LD>(kq.PAx, kq.PAx + CDx, o2q, sl + NH);
+          hermite_E<T, LC, LD>(kq.PAy, kq.PAy + CDy, o2q, sl + NH + EC);
+          hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CDz, o2q, sl + NH + 2 * EC);
+          const T r = Prec<T>::rsq(bp.p + kq.p);
+          const T alpha = bp.p * kq.p * r * r;
+          const T pref = T(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+          prim_R_scaled<T, P::L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, pref, bv, sl);
+        }
+        __syncwarp(gmask);
+        for (int s = 0; s < nv; ++s) {
+          const T* Rs = slots + s * P::SLOT;
+          const T* Es = Rs + NH;
+#pragma unroll
+          for (int k = 0; k < CK; ++k) {
+            const int kc = gl + k * GS;
+            if (kc < NCD) {
+              int cx, cy, cz, dx, dy, dz;
+              cart_pows_rt(LC, kc / ND, cx, cy, cz);
+              cart_pows_rt(LD, kc % ND, dx, dy, dz);
+              for (int tau = 0; tau <= cx + dx; ++tau) {
+                const T ex = Es[(cx * (LD + 1) + dx) * NTC + tau];
+                for (int nu = 0; nu <= cy + dy; ++nu) {
+                  const T exy = ex * Es[EC + (cy * (LD + 1) + dy) * NTC + nu];
+                  for (int phi = 0; phi <= cz + dz; ++phi) {
+                    T e2 = exy * Es[2 * EC + (cz * (LD + 1) + dz) * NTC + phi];
+                    if ((tau + nu + phi) & 1) e2 = -e2;
+                    // R index of (t+tau, u+nu, v+phi) = T3(n0 + sig) + T2(m0 + mu) + v + phi
+                    const int sig = tau + nu + phi, mu = nu + phi;
+                    int t3[LAB + 1], t2[LAB + 1];
+#pragma unroll
+                    for (int x = 0; x <= LAB; ++x) {
+                      const int nn = x + sig, mm = x + mu;
+                      t3[x] = nn * (nn + 1) * (nn + 2) / 6;
+                      t2[x] = mm * (mm + 1) / 2 + phi;
+                    }
+#pragma unroll
+                    for (int n = 0; n <= LAB; ++n)
+#pragma unroll
+                      for (int m = 0; m <= n; ++m)
+#pragma unroll
+                        for (int v = 0; v <= m; ++v)
+                          W[hidx(n - m, m - v, v) * CK + k] += e2 * Rs[t3[n] + t2[m] + v];
+                  }
+                }
+              }
+            }
+          }
+        }
+        __syncwarp(gmask);
+      }
+      // bra transform of this bra primitive into the contracted block
+#pragma unroll
+      for (int k = 0; k < CK; ++k) {
+        const int kc = gl + k * GS;
+        if (kc < NCD) {
+#pragma unroll
+          for (int ab = 0; ab < NAB; ++ab) {
+            const int ia = ab / NB, ib = ab % NB;
+            const int ax = cart_pow(LA, ia, 0), ay = cart_pow(LA, ia, 1), az = cart_pow(LA, ia, 2);
+            const int bx = cart_pow(LB, ib, 0), by = cart_pow(LB, ib, 1), bz = cart_pow(LB, ib, 2);
+            T acc = T(0);
+#pragma unroll
+            for (int t = 0; t <= ax + bx; ++t)
+#pragma unroll
+              for (int u = 0; u <= ay + by; ++u) {
+                const T exy = Eab[(ax * (LB + 1) + bx) * NTA + t] * Eab[EA + (ay * (LB + 1) + by) * NTA + u];
+#pragma unroll
+                for (int v = 0; v <= az + bz; ++v)
+                  acc += exy * Eab[2 * EA + (az * (LB + 1) + bz) * NTA + v] * W[hidx(t, u, v) * CK + k];
+              }
+            Gs[ab * NCD + kc] += bp.K * acc;
+          }
+        }
+      }
+      __syncwarp(gmask);
+    }
+    digest_coop<T, LA, LB, LC, LD>(a, bra, ket, gl, GS, Gs);
+    __syncwarp(gmask);
+  }
+}

@@ -1265,7 +1265,7 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table
   if (st) return st;
   cudaStream_t s = (cudaStream_t)o->stream;
   if ((st = prepare(b, D, o, s))) return st;
-  static const int cand[] = {1, 2, 4, 8, 16};
+  static const int cand[] = {1, 2, 4, 8};
   cudaEvent_t e0, e1;
   ADFT_CUDA(cudaEventCreate(&e0));
   ADFT_CUDA(cudaEventCreate(&e1));

@@ -862,8 +862,11 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
     }
     const long long item = (long long)base + lane;
     if (item < total) {
-      const long long qi = item / C.nchunk;
-      const int chunk = (int)(item - qi * C.nchunk);
+      // chunk-major order: the lanes of a warp share one ket chunk (uniform
+      // component loops) and take consecutive quartets
+      const long long nq = total / C.nchunk;
+      const int chunk = (int)(item / nq);
+      const long long qi = item - (long long)chunk * nq;
       int bra, ket;
       decode_quartet(a, qi, bra, ket);
       quartet_block_rt<T, S>(C, a.bv, bra, ket, chunk, G);
@@ -916,6 +919,8 @@ static __global__ void __launch_bounds__(JK_THREADS) k_prim_schwarz(BasisView bv
 
 #endif  // ADFT_ERI_SCHWARZ
 
+#include "adft_coop.cuh"
+
 // ---------------------------------------------------------------------------
 // dispatch: one launcher per (X, Y) class pair, X >= Y.  The launchers are
 // explicitly instantiated in several translation units (adft_eri_*.cu) so
@@ -931,6 +936,16 @@ cudaError_t launch_one(const JKLaunch& a, int grid, cudaStream_t s) {
     return cudaErrorInvalidValue;
   } else if constexpr (is_small_class(LA, LB, LC, LD)) {
     k_jk<T, LA, LB, LC, LD><<<grid, JK_THREADS, 0, s>>>(a);
+  } else if constexpr (CoopPlan<T, LA, LB, LC, LD>::fits) {
+    using P = CoopPlan<T, LA, LB, LC, LD>;
+    static bool configured = false;  // one attribute call per instantiation
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(k_jk_coop<T, LA, LB, LC, LD>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    k_jk_coop<T, LA, LB, LC, LD><<<grid, 32 * P::WARPS, P::SMEM, s>>>(a);
   } else {
     k_jk_generic<T, LA, LB, LC, LD><<<grid, JK_THREADS, 0, s>>>(a);
   }

@@ -1,6 +1,7 @@
 // Class-pair ERI kernels (FP64 band), bra classes [9]: explicit
 // instantiations of the launchers of adft_eri.cuh, compiled in parallel with the
-// other groups.
+// other groups; also the Schwarz-bound kernels.
+#define ADFT_ERI_SCHWARZ
 #include "adft_eri.cuh"
 
 namespace adft {
@@ -15,5 +16,22 @@ template cudaError_t launch_one<double, 9, 6>(const JKLaunch&, int, cudaStream_t
 template cudaError_t launch_one<double, 9, 7>(const JKLaunch&, int, cudaStream_t);
 template cudaError_t launch_one<double, 9, 8>(const JKLaunch&, int, cudaStream_t);
 template cudaError_t launch_one<double, 9, 9>(const JKLaunch&, int, cudaStream_t);
+
+cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s) {
+  if (X < 0 || X >= NCLS) return cudaErrorInvalidValue;
+  const int blocks = (n + JK_THREADS - 1) / JK_THREADS;
+  const RtClass C = make_rt_class(cls_la(X), cls_lb(X), cls_la(X), cls_lb(X));
+  if (blocks > 0) k_schwarz_generic<<<blocks, JK_THREADS, 0, s>>>(bv, C, first, n, Q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, const int* pp_pair, int npp_class,
+                                double* Qp, cudaStream_t s) {
+  if (X < 0 || X >= NCLS) return cudaErrorInvalidValue;
+  const int blocks = (npp_class + JK_THREADS - 1) / JK_THREADS;
+  const RtClass C = make_rt_class(cls_la(X), cls_lb(X), cls_la(X), cls_lb(X));
+  if (blocks > 0 && n > 0) k_prim_schwarz<<<blocks, JK_THREADS, 0, s>>>(bv, C, first, n, pp_pair, Qp);
+  return cudaGetLastError();
+}
 
 }  // namespace adft

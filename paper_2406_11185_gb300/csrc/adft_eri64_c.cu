@@ -1,32 +1,10 @@
-// Class-pair ERI kernels (FP64 band), bra classes [0, 1, 2, 3, 4, 5, 6]: explicit
+// Class-pair ERI kernels (FP64 band), bra classes [6]: explicit
 // instantiations of the launchers of adft_eri.cuh, compiled in parallel with the
-// other groups; also the Schwarz-bound kernels.
-#define ADFT_ERI_SCHWARZ
+// other groups.
 #include "adft_eri.cuh"
 
 namespace adft {
 
-template cudaError_t launch_one<double, 0, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 1, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 1, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 2, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 2, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 2, 2>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 3, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 3, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 3, 2>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 3, 3>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 2>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 3>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 4>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 5, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 5, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 5, 2>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 5, 3>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 5, 4>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 5, 5>(const JKLaunch&, int, cudaStream_t);
 template cudaError_t launch_one<double, 6, 0>(const JKLaunch&, int, cudaStream_t);
 template cudaError_t launch_one<double, 6, 1>(const JKLaunch&, int, cudaStream_t);
 template cudaError_t launch_one<double, 6, 2>(const JKLaunch&, int, cudaStream_t);
@@ -34,22 +12,5 @@ template cudaError_t launch_one<double, 6, 3>(const JKLaunch&, int, cudaStream_t
 template cudaError_t launch_one<double, 6, 4>(const JKLaunch&, int, cudaStream_t);
 template cudaError_t launch_one<double, 6, 5>(const JKLaunch&, int, cudaStream_t);
 template cudaError_t launch_one<double, 6, 6>(const JKLaunch&, int, cudaStream_t);
-
-cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s) {
-  if (X < 0 || X >= NCLS) return cudaErrorInvalidValue;
-  const int blocks = (n + JK_THREADS - 1) / JK_THREADS;
-  const RtClass C = make_rt_class(cls_la(X), cls_lb(X), cls_la(X), cls_lb(X));
-  if (blocks > 0) k_schwarz_generic<<<blocks, JK_THREADS, 0, s>>>(bv, C, first, n, Q);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, const int* pp_pair, int npp_class,
-                                double* Qp, cudaStream_t s) {
-  if (X < 0 || X >= NCLS) return cudaErrorInvalidValue;
-  const int blocks = (npp_class + JK_THREADS - 1) / JK_THREADS;
-  const RtClass C = make_rt_class(cls_la(X), cls_lb(X), cls_la(X), cls_lb(X));
-  if (blocks > 0 && n > 0) k_prim_schwarz<<<blocks, JK_THREADS, 0, s>>>(bv, C, first, n, pp_pair, Qp);
-  return cudaGetLastError();
-}
 
 }  // namespace adft
