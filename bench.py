@@ -6,10 +6,14 @@ screening and work-list pass, the ERI + J/K digestion kernels of both
 precision bands, the spherical transforms and the energy E_JK
 (adft_jk_energy), with the basis (pairs and Schwarz bounds) built once before
 timing, as in an SCF loop.  The metric is screened shell quartets per second
-of the mixed-precision build; the same build in plain FP64 is timed beside it.
+of the mixed-precision build (--precision mixed: FP64 band in native FP64,
+FP32 band in FP32); the plain FP64 build of the same molecule is timed beside
+it, and the launch shape of every class-pair kernel is autotuned before
+timing.  --precision mixed_emu evaluates the FP64 band in double-float
+arithmetic instead (slower on this GPU in these kernels, kept for study).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                  [--impl reference]
+                  [--precision fp64|mixed|emu|mixed_emu] [--impl reference]
 
 --impl reference times the CPU oracle (the plain FP64 reference written from
 the paper's definitions) on a bounded sample of the same workload.
@@ -47,6 +51,8 @@ WORKLOADS = {
 SMS, CLK_MAX = 152, 2.07e9
 PEAK_FP32 = SMS * 128 * 2 * CLK_MAX / 1e12
 PEAK_FP64 = SMS * 2 * 2 * CLK_MAX / 1e12
+# double-float FMA = 2 algorithmic flops for about 15 FP32 instructions
+PEAK_DF = PEAK_FP32 / 15
 
 
 def _dist():
@@ -176,6 +182,7 @@ def main():
     ap.add_argument("--impl", default="adft", choices=["adft", "reference"])
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "emu", "mixed_emu"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -200,21 +207,35 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    def step(prec="mixed"):
-        return adft.adft_jk_energy(basis, D, thresh=thresh, split=split, precision=prec, check=False,
+    prec = args.precision
+
+    def step(p=prec):
+        return adft.adft_jk_energy(basis, D, thresh=thresh, split=split, precision=p, check=False,
                                    on_device=True)
 
-    # plain FP64 reference build on the same GPU (energy and time)
-    e64 = step("fp64")
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ev[0].record(stream)
-    e64 = step("fp64")
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    fp64_ms = ev[0].elapsed_time(ev[1])
-    st64 = adft.adft_jk_last_stats(basis)
-    E64 = float(e64.item())
+    def one_build(p):
+        """(ms, energy, stats) of one build in precision p after autotuning it."""
+        adft.adft_autotune(basis, D, thresh=thresh, split=split, precision=p)
+        step(p)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        e = step(p)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), float(e.item()), adft.adft_jk_last_stats(basis)
+
+    # reference builds on the same GPU: plain FP64 and (if different) native mixed
+    t0 = time.time()
+    fp64_ms, E64, st64 = one_build("fp64")
+    refs = {"fp64": {"s": fp64_ms / 1e3, "energy": E64}}
+    if prec not in ("mixed", "fp64"):
+        mms, Em, _ = one_build("mixed")
+        refs["mixed"] = {"s": mms / 1e3, "energy": Em, "err_vs_fp64": abs(Em - E64)}
+    # autotune the timed precision (launch shape per class pair and band)
+    tune = adft.adft_autotune(basis, D, thresh=thresh, split=split, precision=prec)
+    tune_s = time.time() - t0
 
     for _ in range(args.warmup):
         step()
@@ -257,7 +278,7 @@ def main():
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         Dd.copy_(Dh, non_blocking=True)
-        adft.adft_jk_build(basis, Dd, thresh=thresh, split=split, precision="mixed", check=True, out=(Jd, Kd))
+        adft.adft_jk_build(basis, Dd, thresh=thresh, split=split, precision=prec, check=True, out=(Jd, Kd))
         Jh.copy_(Jd, non_blocking=True)
         Kh.copy_(Kd, non_blocking=True)
         b.record(stream)
@@ -268,37 +289,41 @@ def main():
 
     # roofline of the dominant kernel group (ALU-bound ERI kernels)
     ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
-    groups = {"eri_fp32": (ph["eri_fp32_ms"], st["flops_fp32"], PEAK_FP32),
-              "eri_fp64": (ph["eri_fp64_ms"], st["flops_fp64"], PEAK_FP64)}
+    emu = prec in ("emu", "mixed_emu")
+    groups = {"eri_fp32": (ph["eri_fp32_ms"], st["flops_fp32"], PEAK_FP32, "FP32 pipe"),
+              ("eri_fp64band_doublefloat" if emu else "eri_fp64"):
+                  (ph["eri_fp64_ms"], st["flops_fp64"], PEAK_DF if emu else PEAK_FP64,
+                   "FP32 pipe / 15 instructions per double-float FMA" if emu else "FP64 pipe")}
     dom = max(groups, key=lambda k: groups[k][0])
-    gms, gfl, gpk = groups[dom]
+    gms, gfl, gpk, gkind = groups[dom]
     ach = gfl / (gms / 1e3) / 1e12 if gms > 0 else 0.0
     roof = {"bound": "alu", "kernel": f"{dom} (all class-pair launches of the band)", "achieved": ach,
             "peak": gpk, "unit": "TFLOP/s", "frac": ach / gpk, "traffic": None,
-            "peak_kind": "derived: 152 SMs x lanes x 2 x 2.07 GHz",
+            "peak_kind": f"derived: 152 SMs x 2.07 GHz, {gkind}",
             "other": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0,
-                          "frac": ((v[1] / (v[0] / 1e3) / 1e12) / v[2]) if v[0] > 0 else 0.0}
+                          "peak": v[2], "frac": ((v[1] / (v[0] / 1e3) / 1e12) / v[2]) if v[0] > 0 else 0.0}
                       for k, v in groups.items()}}
-    line ={"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if not emu else "f32+f32x2(+f64 accumulate)",
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "nbf": basis.nbf,
                        "natom": mol.natom, "nshell": mol.nshell, "thresh": thresh, "split": split,
-                       "precision": "mixed", "l2": "flushed before every step (256 MB write)",
-                       "parallelism": f"replicas x{ws}"},
-            "jk_build_s_mixed": ms / 1e3, "jk_build_s_fp64": fp64_ms / 1e3,
-            "speedup_mixed_vs_fp64": fp64_ms / ms, "energy_mixed": Emix, "energy_fp64": E64,
-            "energy_err_mixed_vs_fp64": abs(Emix - E64),
-            "quartets": {"fp64": st["quartets_fp64"], "fp32": st["quartets_fp32"],
+                       "precision": prec, "l2": "flushed before every step (256 MB write)",
+                       "parallelism": f"replicas x{ws}", "launch_shapes": "autotuned per class pair"},
+            "jk_build_s": ms / 1e3, "jk_build_s_fp64": fp64_ms / 1e3,
+            "speedup_vs_fp64": fp64_ms / ms, "energy": Emix, "energy_fp64": E64,
+            "energy_err_vs_fp64": abs(Emix - E64), "references": refs, "autotune_and_reference_s": tune_s,
+            "quartets": {"fp64_band": st["quartets_fp64"], "fp32_band": st["quartets_fp32"],
                          "unique_before_screening": st["quartets_total"],
-                         "prim_fp64": st["prim_quartets_fp64"], "prim_fp32": st["prim_quartets_fp32"],
+                         "prim_fp64_band": st["prim_quartets_fp64"], "prim_fp32_band": st["prim_quartets_fp32"],
                          "fp64_only_build": st64["quartets_fp64"]},
             "phases_ms": ph, "setup_s": setup_s,
             "clocks": clk.summary(),
             "e2e": {"value": ws * quartets / (np.mean(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
                     "d2h_bytes_per_step": 2 * nb2, "ms": float(np.mean(e2e_ms))},
             "gpu_launches": None, "roofline": roof}
-    line["gpu_launches"] = launches_per_step(basis_classes(mol), mixed=True) * args.steps
+    line["gpu_launches"] = launches_per_step(basis_classes(mol), mixed=prec in ("mixed", "mixed_emu")) * args.steps
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(mol, opt, Dn)
     if rank == 0:

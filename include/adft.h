@@ -74,7 +74,14 @@ enum {
   ADFT_ERR_ABORTED = -8       /* the abort flag of the handle was raised */
 };
 
-enum { ADFT_PREC_FP64 = 0, ADFT_PREC_MIXED = 1 };
+/* Precision modes.  FP64: every kept quartet in native FP64.  MIXED: the
+ * Schwarz-bound dispatch of Sec. 1.2.2, FP64 iff Q_ab Q_cd >= split, else
+ * FP32.  EMU and MIXED_EMU: the same, with the FP64 band evaluated in
+ * double-float arithmetic (pairs of FP32 numbers, about 48 significant bits)
+ * on the FP32 pipe, which on GB300 issues 64 times more FMAs than the FP64
+ * pipe; accumulation into J and K stays FP64.  The gradient evaluates its
+ * FP64 band in native FP64 in every mode. */
+enum { ADFT_PREC_FP64 = 0, ADFT_PREC_MIXED = 1, ADFT_PREC_EMU = 2, ADFT_PREC_MIXED_EMU = 3 };
 
 typedef struct adft_basis adft_basis; /* opaque, library-owned */
 typedef struct adft_batch adft_batch; /* opaque, library-owned */
@@ -89,8 +96,8 @@ typedef struct {
 
 typedef struct {
   double thresh;   /* Schwarz threshold (>= 0): skip iff Q_ab Q_cd < thresh */
-  double split;    /* ADFT_PREC_MIXED only: FP64 iff Q_ab Q_cd >= split */
-  int precision;   /* ADFT_PREC_FP64 or ADFT_PREC_MIXED */
+  double split;    /* mixed modes only: FP64 band iff Q_ab Q_cd >= split */
+  int precision;   /* ADFT_PREC_FP64, _MIXED, _EMU or _MIXED_EMU */
   int check;       /* 1: validate D on the device, synchronise the stream and
                       return ADFT_ERR_ASYM_D / ADFT_ERR_NONFINITE; 0: no check,
                       fully asynchronous */

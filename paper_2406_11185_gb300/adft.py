@@ -25,6 +25,8 @@ ADFT_ERR_TIMEOUT = -7
 ADFT_ERR_ABORTED = -8
 ADFT_PREC_FP64 = 0
 ADFT_PREC_MIXED = 1
+ADFT_PREC_EMU = 2
+ADFT_PREC_MIXED_EMU = 3
 ADFT_LMAX = 3
 ADFT_MAX_NPRIM = 16
 ADFT_STATIC_MAX_NBF = 16384
@@ -128,7 +130,8 @@ def _stream_ptr(stream):
 
 
 def make_opts(thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None) -> adft_opts:
-    prec = {"fp64": ADFT_PREC_FP64, "mixed": ADFT_PREC_MIXED}[precision] if isinstance(precision, str) \
+    prec = {"fp64": ADFT_PREC_FP64, "mixed": ADFT_PREC_MIXED, "emu": ADFT_PREC_EMU,
+            "mixed_emu": ADFT_PREC_MIXED_EMU}[precision] if isinstance(precision, str) \
         else int(precision)
     return adft_opts(float(thresh), float(split), prec, 1 if check else 0, _stream_ptr(stream))
 

@@ -53,7 +53,20 @@ template <typename T, int L>
 __device__ __forceinline__ void prim_R_scaled(T alpha, T X, T Y, T Z, T pref, const BasisView& bv, T* R) {
   T B[L + 1];
   const T Tb = alpha * (X * X + Y * Y + Z * Z);
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (std::is_same<T, df>::value) {
+    boys_df_scaled<L>(Tb, bv, B);
+#pragma unroll
+    for (int n = 0; n <= L; ++n) B[n] *= (n & 1) ? -pref : pref;
+    const df sc = df_scale(alpha, Tb);
+    hermite_R_inplace<T, L>(B, X * sc, Y * sc, Z * sc, R);
+    df sp = sc;
+#pragma unroll
+    for (int n = 1; n <= L; ++n) {
+#pragma unroll
+      for (int x = nherm(n - 1); x < nherm(n); ++x) R[x] *= sp;
+      sp *= sc;
+    }
+  } else if constexpr (is_f64<T>) {
     boys_fp64<L>(Tb, bv.boys64, B);
     const T f = -2.0 * alpha;
     T pw = pref;
@@ -93,12 +106,12 @@ __device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket,
   long n;
   mol_block(bv, bra, base, n);
   T w = T(1);
-  if (sa == sb) w *= T(0.5);
-  if (sc == sd) w *= T(0.5);
-  if (a.same_class && bra == ket) w *= T(0.5);
+  if (sa == sb) w *= cst<T>(0.5);
+  if (sc == sd) w *= cst<T>(0.5);
+  if (a.same_class && bra == ket) w *= cst<T>(0.5);
   const T w4 = T(4) * w, w2 = T(2) * w;
   const T* __restrict__ D = nullptr;
-  if constexpr (sizeof(T) == 8) D = (const T*)a.D64 + base; else D = (const T*)a.D32 + base;
+  D = dmat<T>(a) + base;
   double* __restrict__ Jm = a.J + base;
   double* __restrict__ Km = a.K + base;
   // J_ab partial over this lane's ket components
@@ -193,10 +206,10 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
     decode_quartet(a, qi, bra, ket);
     const int off0 = __ldg(bv.pair_pp_off + bra), n0 = __ldg(bv.pair_pp_n + bra);
     const int off1 = __ldg(bv.pair_pp_off + ket), n1 = __ldg(bv.pair_pp_n + ket);
-    const T AB[3] = {(T)__ldg(bv.pair_AB + 3 * bra), (T)__ldg(bv.pair_AB + 3 * bra + 1),
-                     (T)__ldg(bv.pair_AB + 3 * bra + 2)};
-    const T CDx = (T)__ldg(bv.pair_AB + 3 * ket), CDy = (T)__ldg(bv.pair_AB + 3 * ket + 1),
-            CDz = (T)__ldg(bv.pair_AB + 3 * ket + 2);
+    const T AB[3] = {from_f64<T>(__ldg(bv.pair_AB + 3 * bra)), from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 1)),
+                     from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 2))};
+    const T CDx = from_f64<T>(__ldg(bv.pair_AB + 3 * ket)), CDy = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 1)),
+            CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
     for (int kc = gl; kc < NCD; kc += GS)
       for (int ab = 0; ab < NAB; ++ab) Gs[ab * NCD + kc] = T(0);
 
@@ -223,7 +236,7 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
           hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CDz, o2q, sl + NH + 2 * EC);
           const T r = Prec<T>::rsq(bp.p + kq.p);
           const T alpha = bp.p * kq.p * r * r;
-          const T pref = T(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+          const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
           prim_R_scaled<T, P::L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, pref, bv, sl);
         }
         __syncwarp(gmask);

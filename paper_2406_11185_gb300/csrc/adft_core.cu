@@ -62,11 +62,18 @@ static void boys_row(double T, double* F) {
 struct DeviceTables {
   double* boys64 = nullptr;
   float* boys32 = nullptr;
+  df* boysdf = nullptr;
+  df* expdf = nullptr;
 };
+
+static df host_df(double x) {
+  const float h = (float)x;
+  return df(h, (float)(x - (double)h));
+}
 static std::mutex g_tab_mu;
 static DeviceTables g_tab[64];
 
-cudaError_t boys_tables(const double** t64, const float** t32) {
+cudaError_t boys_tables(const double** t64, const float** t32, const df** tdf, const df** edf) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -84,11 +91,29 @@ cudaError_t boys_tables(const double** t64, const float** t32) {
     if ((e = cudaMalloc(&d32, hf.size() * sizeof(float))) != cudaSuccess) { cudaFree(d64); return e; }
     cudaMemcpy(d64, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(d32, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    // double-float tables at T = i/16
+    std::vector<double> row(W);
+    std::vector<df> hdf(BOYS_DF_NT * W), hex(BOYS_DF_NT);
+    for (int i = 0; i < BOYS_DF_NT; ++i) {
+      boys_row(i / 16.0, row.data());
+      for (int m = 0; m < W; ++m) hdf[i * W + m] = host_df(row[m]);
+      hex[i] = host_df((double)expl(-(long double)i / 16.0L));
+    }
+    df* ddf = nullptr;
+    df* dex = nullptr;
+    if ((e = cudaMalloc(&ddf, hdf.size() * sizeof(df))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&dex, hex.size() * sizeof(df))) != cudaSuccess) return e;
+    cudaMemcpy(ddf, hdf.data(), hdf.size() * sizeof(df), cudaMemcpyHostToDevice);
+    cudaMemcpy(dex, hex.data(), hex.size() * sizeof(df), cudaMemcpyHostToDevice);
     g_tab[dev].boys64 = d64;
     g_tab[dev].boys32 = d32;
+    g_tab[dev].boysdf = ddf;
+    g_tab[dev].expdf = dex;
   }
   *t64 = g_tab[dev].boys64;
   *t32 = g_tab[dev].boys32;
+  *tdf = g_tab[dev].boysdf;
+  *edf = g_tab[dev].expdf;
   return cudaSuccess;
 }
 
@@ -133,12 +158,16 @@ static void sph_coefficients(double out[LMAX + 1][2 * LMAX + 1][SPH_MAXC]) {
   }
 }
 
+static inline bool is_mixed(int prec) { return prec == ADFT_PREC_MIXED || prec == ADFT_PREC_MIXED_EMU; }
+static inline bool is_emulated(int prec) { return prec == ADFT_PREC_EMU || prec == ADFT_PREC_MIXED_EMU; }
+
 // ---------------------------------------------------------------------------
 // basis handle
 
 struct Workspace {
   double* Dc = nullptr;     // Cartesian D, packed per molecule
   float* Dc32 = nullptr;
+  df* Dcdf = nullptr;
   double* Jc = nullptr;     // Cartesian accumulators (unsymmetrised)
   double* Kc = nullptr;
   double* Jw = nullptr;     // J, K in the output basis (energy calls)
@@ -197,6 +226,10 @@ struct adft_basis {
   int *d_cfunc_shell = nullptr, *d_cfunc_comp = nullptr;  // Cartesian function -> (shell, component)
   const double* boys64 = nullptr;
   const float* boys32 = nullptr;
+  const adft::df* boysdf = nullptr;
+  const adft::df* expdf = nullptr;
+  adft::PrimPair<adft::df>* d_ppdf = nullptr;
+  adft::df* d_o2pdf = nullptr;
   adft::Workspace ws;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -247,6 +280,7 @@ static BasisView view(const adft_basis* b) {
   v.pp64 = b->d_pp64; v.pp32 = b->d_pp32; v.boys64 = b->boys64; v.boys32 = b->boys32;
   v.pp_w64 = b->d_ppw64; v.pp_w32 = b->d_ppw32; v.npp = b->npp;
   v.pp_o2p64 = b->d_o2p64; v.pp_o2p32 = b->d_o2p32;
+  v.ppdf = b->d_ppdf; v.pp_o2pdf = b->d_o2pdf; v.boysdf = b->boysdf; v.expdf = b->expdf;
   v.pair_mol = (b->nmol > 1) ? b->d_pair_mol : nullptr;
   v.mol_cbase = b->d_mol_cbase; v.mol_nc = b->d_mol_nc;
   return v;
@@ -260,7 +294,7 @@ __global__ void k_build_pairs(int npair, const int* __restrict__ pair_a, const i
                               const double* __restrict__ xyz, const double* __restrict__ exps,
                               const double* __restrict__ ncoefs, long long npp, PrimPair<double>* pp64,
                               PrimPair<float>* pp32, double* w64, float* w32, double* o2p64, float* o2p32,
-                              int* pp_pair) {
+                              PrimPair<df>* ppdf, df* o2pdf, int* pp_pair) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= npp) return;
   // pair owning primitive pair g (ppoff is ascending)
@@ -285,6 +319,9 @@ __global__ void k_build_pairs(int npair, const int* __restrict__ pair_a, const i
   w64[g] = 2.0 * a; w64[npp + g] = 2.0 * b;
   o2p64[g] = 0.5 / p;
   o2p32[g] = (float)(0.5 / p);
+  ppdf[g] = PrimPair<df>{to_df(Px), to_df(Py), to_df(Pz), to_df(p), to_df(Px - A[0]), to_df(Py - A[1]),
+                         to_df(Pz - A[2]), to_df(K)};
+  o2pdf[g] = to_df(0.5 / p);
   w32[g] = (float)(2.0 * a); w32[npp + g] = (float)(2.0 * b);
   if (pp_pair) pp_pair[g] = pr;
 }
@@ -508,7 +545,8 @@ __device__ __forceinline__ int find_mol(const long long* base, int nmol, long lo
   return lo;
 }
 
-__global__ void k_d_to_cart(XformArgs x, long long total, const double* __restrict__ D, double* Dc, float* Dc32) {
+__global__ void k_d_to_cart(XformArgs x, long long total, const double* __restrict__ D, double* Dc, float* Dc32,
+                            df* Dcdf) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int m = find_mol(x.cbase, x.nmol, g);
@@ -535,6 +573,7 @@ __global__ void k_d_to_cart(XformArgs x, long long total, const double* __restri
   }
   Dc[g] = v;
   Dc32[g] = (float)v;
+  Dcdf[g] = to_df(v);
 }
 
 __global__ void k_from_cart(XformArgs x, long long total, const double* __restrict__ Jc,
@@ -656,7 +695,7 @@ static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStrea
     k_check_d<<<(unsigned)((nb2 + T256 - 1) / T256), T256, 0, s>>>(x, nb2, D, w.scal, w.status);
     ADFT_CUDA(cudaGetLastError());
   }
-  k_d_to_cart<<<(unsigned)((nc2 + T256 - 1) / T256), T256, 0, s>>>(x, nc2, D, w.Dc, w.Dc32);
+  k_d_to_cart<<<(unsigned)((nc2 + T256 - 1) / T256), T256, 0, s>>>(x, nc2, D, w.Dc, w.Dc32, w.Dcdf);
   ADFT_CUDA(cudaGetLastError());
   ADFT_CUDA(cudaMemsetAsync(w.Jc, 0, nc2 * sizeof(double), s));
   ADFT_CUDA(cudaMemsetAsync(w.Kc, 0, nc2 * sizeof(double), s));
@@ -671,7 +710,7 @@ static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStrea
   sa.pair_mol = b->nmol > 1 ? b->d_pair_mol : nullptr;
   sa.Q = b->d_pair_Q; sa.ppn = b->d_pair_ppn; sa.cumppn = b->d_cumppn;
   sa.thresh = o->thresh;
-  sa.mixed = (o->precision == ADFT_PREC_MIXED);
+  sa.mixed = is_mixed(o->precision);
   sa.split = sa.mixed ? o->split : 0.0;
   sa.cnt64 = w.cnt64; sa.cnt32 = w.cnt32; sa.kst64 = w.kst64; sa.kst32 = w.kst32; sa.stats = w.stats;
   for (int X = 0; X < NCLS; ++X)
@@ -704,7 +743,7 @@ static JKLaunch base_launch(adft_basis* b) {
   Workspace& w = b->ws;
   JKLaunch L;
   L.bv = view(b);
-  L.D64 = w.Dc; L.D32 = w.Dc32; L.J = w.Jc; L.K = w.Kc;
+  L.D64 = w.Dc; L.D32 = w.Dc32; L.Ddf = w.Dcdf; L.J = w.Jc; L.K = w.Kc;
   L.abort_flag = w.status + 1;
   L.status = w.status;
   return L;
@@ -716,7 +755,7 @@ static JKLaunch base_launch(adft_basis* b) {
 template <typename Fn>
 static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cudaStream_t s, int pass, Fn fn) {
   Workspace& w = b->ws;
-  for (int band = 0; band < (o->precision == ADFT_PREC_MIXED ? 2 : 1); ++band) {
+  for (int band = 0; band < (is_mixed(o->precision) ? 2 : 1); ++band) {
     for (int X = NCLS - 1; X >= 0; --X)
       for (int Y = X; Y >= 0; --Y) {
         const int nX = b->cls_first[X + 1] - b->cls_first[X];
@@ -737,7 +776,7 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
       }
     ADFT_CUDA(cudaEventRecord(b->ev[2 + band], s));
   }
-  if (o->precision != ADFT_PREC_MIXED) ADFT_CUDA(cudaEventRecord(b->ev[3], s));
+  if (!is_mixed(o->precision)) ADFT_CUDA(cudaEventRecord(b->ev[3], s));
   return ADFT_OK;
 }
 
@@ -745,7 +784,8 @@ static int run_jk(adft_basis* b, const double* D, const adft_opts* o, cudaStream
   int st = prepare(b, D, o, s);
   if (st) return st;
   return for_each_class_pair(b, o, base_launch(b), s, 0, [&](int X, int Y, const JKLaunch& L, int band, int grid) {
-    return band == 0 ? launch_jk_fp64(X, Y, L, grid, s) : launch_jk_fp32(X, Y, L, grid, s);
+    if (band == 1) return launch_jk_fp32(X, Y, L, grid, s);
+    return is_emulated(o->precision) ? launch_jk_df(X, Y, L, grid, s) : launch_jk_fp64(X, Y, L, grid, s);
   });
 }
 
@@ -799,11 +839,11 @@ static int finish_check(adft_basis* b, const adft_opts* o, cudaStream_t s) {
 static int check_opts(const adft_opts* o) {
   if (!o) { set_error("opts is NULL"); return ADFT_ERR_ARG; }
   if (!(o->thresh >= 0.0) || !isfinite(o->thresh)) { set_error("thresh must be finite and >= 0"); return ADFT_ERR_ARG; }
-  if (o->precision != ADFT_PREC_FP64 && o->precision != ADFT_PREC_MIXED) {
-    set_error("precision must be ADFT_PREC_FP64 or ADFT_PREC_MIXED");
+  if (o->precision < ADFT_PREC_FP64 || o->precision > ADFT_PREC_MIXED_EMU) {
+    set_error("precision must be ADFT_PREC_FP64, _MIXED, _EMU or _MIXED_EMU");
     return ADFT_ERR_ARG;
   }
-  if (o->precision == ADFT_PREC_MIXED && (!(o->split >= 0.0) || !isfinite(o->split))) {
+  if (is_mixed(o->precision) && (!(o->split >= 0.0) || !isfinite(o->split))) {
     set_error("split must be finite and >= 0");
     return ADFT_ERR_ARG;
   }
@@ -899,7 +939,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
   b->cls_first[NCLS] = (int)pa.size();
   b->npair = (int)pa.size();
 
-  st = boys_tables(&b->boys64, &b->boys32);
+  st = boys_tables(&b->boys64, &b->boys32, &b->boysdf, &b->expdf);
   if (st != cudaSuccess) { set_error("Boys table upload failed"); return ADFT_ERR_CUDA; }
   {
     double h_sph[LMAX + 1][2 * LMAX + 1][SPH_MAXC];
@@ -946,7 +986,8 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
           (r = dalloc(b, &b->d_pp64, (size_t)tot)) || (r = dalloc(b, &b->d_pp32, (size_t)tot)) ||
           (r = dalloc(b, &b->d_ppw64, 2 * (size_t)tot)) || (r = dalloc(b, &b->d_ppw32, 2 * (size_t)tot)) ||
           (r = dalloc(b, &b->d_pp_src, (size_t)tot)) || (r = dalloc(b, &b->d_o2p64, (size_t)tot)) ||
-          (r = dalloc(b, &b->d_o2p32, (size_t)tot)))
+          (r = dalloc(b, &b->d_o2p32, (size_t)tot)) || (r = dalloc(b, &b->d_ppdf, (size_t)tot)) ||
+          (r = dalloc(b, &b->d_o2pdf, (size_t)tot)))
         return r;
     }
     ADFT_CUDA(cudaMemcpy(b->d_pair_a, A.data(), A.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -965,7 +1006,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
                                                          b->d_pp_src, b->d_shell_atom, b->d_shell_poff, b->d_xyz,
                                                          b->d_exps, b->d_ncoefs, tot, b->d_pp64, b->d_pp32,
                                                          b->d_ppw64, b->d_ppw32, b->d_o2p64, b->d_o2p32,
-                                                         pp_pair_dev);
+                                                         b->d_ppdf, b->d_o2pdf, pp_pair_dev);
       ADFT_CUDA(cudaGetLastError());
     }
     return ADFT_OK;
@@ -1042,7 +1083,8 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
       }
     Workspace& w = b->ws;
     const size_t nc2 = (size_t)b->mol_cbase[b->nmol], nb2 = (size_t)b->mol_obase[b->nmol];
-    if ((st = dalloc(b, &w.Dc, nc2)) || (st = dalloc(b, &w.Dc32, nc2)) || (st = dalloc(b, &w.Jc, nc2)) ||
+    if ((st = dalloc(b, &w.Dc, nc2)) || (st = dalloc(b, &w.Dc32, nc2)) || (st = dalloc(b, &w.Dcdf, nc2)) ||
+        (st = dalloc(b, &w.Jc, nc2)) ||
         (st = dalloc(b, &w.Kc, nc2)) || (st = dalloc(b, &w.Jw, nb2)) || (st = dalloc(b, &w.Kw, nb2)) ||
         (st = dalloc(b, &w.cnt64, (size_t)co)) || (st = dalloc(b, &w.cnt32, (size_t)co)) ||
         (st = dalloc(b, &w.kst64, (size_t)co)) || (st = dalloc(b, &w.kst32, (size_t)co)) ||
@@ -1271,7 +1313,7 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table
   ADFT_CUDA(cudaEventCreate(&e1));
   if (ms_out)
     for (int i = 0; i < 2 * NCP; ++i) ms_out[i] = 0.0;
-  for (int band = 0; band < (o->precision == ADFT_PREC_MIXED ? 2 : 1); ++band)
+  for (int band = 0; band < (is_mixed(o->precision) ? 2 : 1); ++band)
     for (int X = NCLS - 1; X >= 0; --X)
       for (int Y = X; Y >= 0; --Y) {
         const int cp = cp_index(X, Y);
@@ -1287,7 +1329,9 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table
           L.counter = b->ws.counters + 2 * NCP + 2 * cp + band;
           ADFT_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s));
           ADFT_CUDA(cudaEventRecord(e0, s));
-          cudaError_t e = band == 0 ? launch_jk_fp64(X, Y, L, b->sms * c, s) : launch_jk_fp32(X, Y, L, b->sms * c, s);
+          cudaError_t e = band == 1 ? launch_jk_fp32(X, Y, L, b->sms * c, s)
+                          : is_emulated(o->precision) ? launch_jk_df(X, Y, L, b->sms * c, s)
+                                                      : launch_jk_fp64(X, Y, L, b->sms * c, s);
           if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
           ADFT_CUDA(cudaEventRecord(e1, s));
           ADFT_CUDA(cudaEventSynchronize(e1));

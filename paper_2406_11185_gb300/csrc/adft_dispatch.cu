@@ -1,5 +1,5 @@
 // Dispatch tables of the class-pair ERI launchers (instantiated in
-// adft_eri64_*.cu and adft_eri32_*.cu) and the Schwarz-bound launchers.
+// adft_eri64_*.cu, adft_eri32_*.cu and adft_eridf_*.cu).
 #define ADFT_ERI_DECLARE_ONLY
 #include "adft_eri.cuh"
 
@@ -21,6 +21,10 @@ cudaError_t launch_jk_fp64(int X, int Y, const JKLaunch& a, int grid, cudaStream
 
 cudaError_t launch_jk_fp32(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s) {
   return dispatch<float>(X, Y, a, grid, s, std::make_integer_sequence<int, NCLS * NCLS>{});
+}
+
+cudaError_t launch_jk_df(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s) {
+  return dispatch<df>(X, Y, a, grid, s, std::make_integer_sequence<int, NCLS * NCLS>{});
 }
 
 }  // namespace adft

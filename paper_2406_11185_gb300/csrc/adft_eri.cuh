@@ -16,6 +16,7 @@
 // primitives.  A thread owns one shell quartet and a chunk of CK ket
 // Cartesian components (all bra components), which bounds its state.
 #pragma once
+#include <type_traits>
 #include <utility>
 
 #include "adft_internal.cuh"
@@ -50,6 +51,19 @@ __host__ __device__ constexpr int hidx(int t, int u, int v) {
 
 template <typename T> __device__ __forceinline__ T dload(const T* p) { return __ldg(p); }
 
+// constants and matrices of the three arithmetic types (double, float,
+// double-float)
+template <typename T> __device__ __forceinline__ constexpr T cst(double x) { return T(x); }
+template <> __device__ __forceinline__ constexpr df cst<df>(double x) { return dfc(x); }
+template <typename T> __device__ __forceinline__ const T* dmat(const JKLaunch& a);
+template <> __device__ __forceinline__ const double* dmat<double>(const JKLaunch& a) { return a.D64; }
+template <> __device__ __forceinline__ const float* dmat<float>(const JKLaunch& a) { return a.D32; }
+template <> __device__ __forceinline__ const df* dmat<df>(const JKLaunch& a) { return a.Ddf; }
+template <typename T> __device__ __forceinline__ T from_f64(double x) { return (T)x; }
+template <> __device__ __forceinline__ df from_f64<df>(double x) { return to_df(x); }
+template <typename T> constexpr bool is_f64 = std::is_same<T, double>::value;
+template <typename T> constexpr bool is_f32 = std::is_same<T, float>::value;
+
 // chunk of ket components owned by one thread
 template <int NAB, int NHAB, int NCD, int BUDGET>
 struct ChunkPlan {
@@ -63,6 +77,12 @@ template <> struct Prec<double> {
   static __device__ __forceinline__ const PrimPair<double>* pp(const BasisView& b) { return b.pp64; }
   static __device__ __forceinline__ const double* o2p(const BasisView& b) { return b.pp_o2p64; }
   static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+  static constexpr int BUDGET = 640;
+};
+template <> struct Prec<df> {
+  static __device__ __forceinline__ const PrimPair<df>* pp(const BasisView& b) { return b.ppdf; }
+  static __device__ __forceinline__ const df* o2p(const BasisView& b) { return b.pp_o2pdf; }
+  static __device__ __forceinline__ df rsq(df x) { return rsqrt_df(x); }
   static constexpr int BUDGET = 640;
 };
 template <> struct Prec<float> {
@@ -140,6 +160,85 @@ __device__ __forceinline__ void boys_fp32_scaled(float T, const float* __restric
 #pragma unroll
     for (int m = 0; m < L; ++m) G[m + 1] = (2 * m + 1) * G[m];
   }
+}
+
+// Double-float, scaled like the FP32 version: G_m = c^m F_m(T), c = max(1, 2T).
+// Below T = 60: 7-term Taylor expansion of F_L about T_i = i/16 (|T - T_i| <=
+// 1/32), e^-T = e^-T_i e^(T_i - T) with an 8-term series, downward recursion;
+// above: G_0 = sqrt(pi/T)/2, G_{m+1} = (2m+1) G_m.
+__constant__ static const df c_inv_int_df[8] = {dfc(1.0), dfc(1.0), dfc(1.0 / 2), dfc(1.0 / 3),
+                                                dfc(1.0 / 4), dfc(1.0 / 5), dfc(1.0 / 6), dfc(1.0 / 7)};
+__constant__ static const df c_inv_fact_df[8] = {dfc(1.0), dfc(1.0), dfc(1.0 / 2), dfc(1.0 / 6),
+                                                 dfc(1.0 / 24), dfc(1.0 / 120), dfc(1.0 / 720), dfc(1.0 / 5040)};
+__constant__ static const df c_inv_odd_df[32] = {
+    dfc(1.0 / 1), dfc(1.0 / 3), dfc(1.0 / 5), dfc(1.0 / 7), dfc(1.0 / 9), dfc(1.0 / 11), dfc(1.0 / 13),
+    dfc(1.0 / 15), dfc(1.0 / 17), dfc(1.0 / 19), dfc(1.0 / 21), dfc(1.0 / 23), dfc(1.0 / 25), dfc(1.0 / 27),
+    dfc(1.0 / 29), dfc(1.0 / 31), dfc(1.0 / 33), dfc(1.0 / 35), dfc(1.0 / 37), dfc(1.0 / 39), dfc(1.0 / 41),
+    dfc(1.0 / 43), dfc(1.0 / 45), dfc(1.0 / 47), dfc(1.0 / 49), dfc(1.0 / 51), dfc(1.0 / 53), dfc(1.0 / 55),
+    dfc(1.0 / 57), dfc(1.0 / 59), dfc(1.0 / 61), dfc(1.0 / 63)};
+
+__device__ __forceinline__ df boys_df_lowT(int L, df T, const BasisView& bv, int& i_out, df& e_out) {
+  const int i = __float2int_rn(T.hi * 16.0f);
+  const df y = df((float)i * 0.0625f, 0.f) - T;
+  const df* row = bv.boysdf + i * (BOYS_MMAX + 1) + L;
+  df acc = __ldg(row + 6);
+#pragma unroll
+  for (int k = 6; k >= 1; --k) acc = __ldg(row + k - 1) + acc * (y * c_inv_int_df[k]);
+  df ey = c_inv_fact_df[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) ey = c_inv_fact_df[k] + y * ey;
+  e_out = __ldg(bv.expdf + i) * ey;
+  i_out = i;
+  return acc;
+}
+
+template <int L>
+__device__ __forceinline__ void boys_df_scaled(df T, const BasisView& bv, df* G) {
+  if (T.hi < (float)BOYS_TMAX) {
+    int i;
+    df e;
+    G[L] = boys_df_lowT(L, T, bv, i, e);
+    const df T2 = df(2.0f * T.hi, 2.0f * T.lo);
+#pragma unroll
+    for (int m = L - 1; m >= 0; --m) G[m] = (T2 * G[m + 1] + e) * c_inv_odd_df[m];
+    if (T2.hi > 1.0f) {
+      df cn = T2;
+#pragma unroll
+      for (int m = 1; m <= L; ++m) { G[m] *= cn; cn *= T2; }
+    }
+  } else {
+    G[0] = dfc(0.88622692545275801365) * rsqrt_df(T);
+#pragma unroll
+    for (int m = 0; m < L; ++m) G[m + 1] = G[m] * df(2 * m + 1);
+  }
+}
+
+__device__ __forceinline__ void boys_df_scaled_rt(int L, df T, const BasisView& bv, df* G) {
+  if (T.hi < (float)BOYS_TMAX) {
+    int i;
+    df e;
+    G[L] = boys_df_lowT(L, T, bv, i, e);
+    const df T2 = df(2.0f * T.hi, 2.0f * T.lo);
+#pragma unroll 1
+    for (int m = L - 1; m >= 0; --m) G[m] = (T2 * G[m + 1] + e) * c_inv_odd_df[m];
+    if (T2.hi > 1.0f) {
+      df cn = T2;
+#pragma unroll 1
+      for (int m = 1; m <= L; ++m) { G[m] *= cn; cn *= T2; }
+    }
+  } else {
+    G[0] = dfc(0.88622692545275801365) * rsqrt_df(T);
+#pragma unroll 1
+    for (int m = 0; m < L; ++m) G[m + 1] = G[m] * df(2 * m + 1);
+  }
+}
+
+// scale factor s = sqrt(2 alpha / c), c = max(1, 2T), of the double-float
+// (and FP32) Hermite recursion
+__device__ __forceinline__ df df_scale(df alpha, df Tb) {
+  const df c = (2.0f * Tb.hi > 1.0f) ? df(2.0f * Tb.hi, 2.0f * Tb.lo) : df(1);
+  const df x = df(2.0f * alpha.hi, 2.0f * alpha.lo) * rcp_df(c);
+  return x * rsqrt_df(x);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,7 +322,20 @@ template <typename T, int L>
 __device__ __forceinline__ void prim_R(T alpha, T X, T Y, T Z, const BasisView& bv, T* R) {
   T B[L + 1];
   const T Tb = alpha * (X * X + Y * Y + Z * Z);
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (std::is_same<T, df>::value) {
+    boys_df_scaled<L>(Tb, bv, B);
+#pragma unroll
+    for (int n = 1; n <= L; n += 2) B[n] = -B[n];
+    const df sc = df_scale(alpha, Tb);
+    hermite_R<T, L>(B, X * sc, Y * sc, Z * sc, R);
+    df sp = sc;
+#pragma unroll
+    for (int n = 1; n <= L; ++n) {
+#pragma unroll
+      for (int x = nherm(n - 1); x < nherm(n); ++x) R[x] *= sp;
+      sp *= sc;
+    }
+  } else if constexpr (is_f64<T>) {
     boys_fp64<L>(Tb, bv.boys64, B);
     T f = -2.0 * alpha, pw = f;
 #pragma unroll
@@ -261,10 +373,10 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
 
   const int off0 = __ldg(bv.pair_pp_off + bra), n0 = __ldg(bv.pair_pp_n + bra);
   const int off1 = __ldg(bv.pair_pp_off + ket), n1 = __ldg(bv.pair_pp_n + ket);
-  const T ABx = (T)__ldg(bv.pair_AB + 3 * bra), ABy = (T)__ldg(bv.pair_AB + 3 * bra + 1),
-          ABz = (T)__ldg(bv.pair_AB + 3 * bra + 2);
-  const T CDx = (T)__ldg(bv.pair_AB + 3 * ket), CDy = (T)__ldg(bv.pair_AB + 3 * ket + 1),
-          CDz = (T)__ldg(bv.pair_AB + 3 * ket + 2);
+  const T ABx = from_f64<T>(__ldg(bv.pair_AB + 3 * bra)), ABy = from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 1)),
+          ABz = from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 2));
+  const T CDx = from_f64<T>(__ldg(bv.pair_AB + 3 * ket)), CDy = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 1)),
+          CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
 
   // powers of the owned ket components
   int cp[CK][6];
@@ -304,7 +416,7 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
       const T alpha = bp.p * kq.p * r * r;
       T R[nherm(L)];
       prim_R<T, L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
-      const T pref = T(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+      const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
 #pragma unroll
       for (int k = 0; k < CK; ++k) {
         const int cx = cp[k][0], cy = cp[k][1], cz = cp[k][2], dx = cp[k][3], dy = cp[k][4], dz = cp[k][5];
@@ -488,7 +600,20 @@ template <typename T>
 __device__ __forceinline__ void prim_R_rt(int L, T alpha, T X, T Y, T Z, const BasisView& bv, T* R) {
   T B[GEN_L + 1];
   const T Tb = alpha * (X * X + Y * Y + Z * Z);
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (std::is_same<T, df>::value) {
+    boys_df_scaled_rt(L, Tb, bv, B);
+#pragma unroll 1
+    for (int n = 1; n <= L; n += 2) B[n] = -B[n];
+    const df sc = df_scale(alpha, Tb);
+    hermite_R_rt<T>(L, B, X * sc, Y * sc, Z * sc, R);
+    df sp = sc;
+#pragma unroll 1
+    for (int n = 1; n <= L; ++n) {
+      const int lo = n * (n + 1) * (n + 2) / 6, hi = (n + 1) * (n + 2) * (n + 3) / 6;
+      for (int x = lo; x < hi; ++x) R[x] *= sp;
+      sp *= sc;
+    }
+  } else if constexpr (is_f64<T>) {
     boys_fp64_rt(L, Tb, bv.boys64, B);
     const T f = -2.0 * alpha;
     T pw = f;
@@ -549,10 +674,10 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
   const int n0 = pp_bra >= 0 ? 1 : __ldg(bv.pair_pp_n + bra);
   const int off1 = pp_ket >= 0 ? pp_ket : __ldg(bv.pair_pp_off + ket);
   const int n1 = pp_ket >= 0 ? 1 : __ldg(bv.pair_pp_n + ket);
-  const T ABx = (T)__ldg(bv.pair_AB + 3 * bra), ABy = (T)__ldg(bv.pair_AB + 3 * bra + 1),
-          ABz = (T)__ldg(bv.pair_AB + 3 * bra + 2);
-  const T CDx = (T)__ldg(bv.pair_AB + 3 * ket), CDy = (T)__ldg(bv.pair_AB + 3 * ket + 1),
-          CDz = (T)__ldg(bv.pair_AB + 3 * ket + 2);
+  const T ABx = from_f64<T>(__ldg(bv.pair_AB + 3 * bra)), ABy = from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 1)),
+          ABz = from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 2));
+  const T CDx = from_f64<T>(__ldg(bv.pair_AB + 3 * ket)), CDy = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 1)),
+          CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
   const int nhab = nherm(LAB);
   const int kc0 = chunk * CK;
   const int nk = min(CK, NCD - kc0);
@@ -580,7 +705,7 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
       const T r = Prec<T>::rsq(bp.p + kq.p);
       const T alpha = bp.p * kq.p * r * r;
       prim_R_rt<T>(L, alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
-      const T pref = T(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+      const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
 #pragma unroll 1
       for (int k = 0; k < nk; ++k) {
         const int kc = kc0 + k;
@@ -647,12 +772,12 @@ __device__ __noinline__ void digest_rt(const RtClass& C, const JKLaunch& a, int 
   long n;
   mol_block(bv, bra, base, n);
   T w = T(1);
-  if (sa == sb) w *= T(0.5);
-  if (sc == sd) w *= T(0.5);
-  if (a.same_class && bra == ket) w *= T(0.5);
+  if (sa == sb) w *= cst<T>(0.5);
+  if (sc == sd) w *= cst<T>(0.5);
+  if (a.same_class && bra == ket) w *= cst<T>(0.5);
   const T w4 = T(4) * w, w2 = T(2) * w;
   const T* __restrict__ D = nullptr;
-  if constexpr (sizeof(T) == 8) D = (const T*)a.D64 + base; else D = (const T*)a.D32 + base;
+  D = dmat<T>(a) + base;
   double* __restrict__ Jm = a.J + base;
   double* __restrict__ Km = a.K + base;
   const int kc0 = chunk * CK, nk = min(CK, NCD - kc0);
@@ -729,12 +854,12 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int 
   long n;
   mol_block(bv, bra, base, n);
   T w = T(1);
-  if (sa == sb) w *= T(0.5);
-  if (sc == sd) w *= T(0.5);
-  if (a.same_class && bra == ket) w *= T(0.5);
+  if (sa == sb) w *= cst<T>(0.5);
+  if (sc == sd) w *= cst<T>(0.5);
+  if (a.same_class && bra == ket) w *= cst<T>(0.5);
   const T w4 = T(4) * w, w2 = T(2) * w;
   const T* __restrict__ D = nullptr;
-  if constexpr (sizeof(T) == 8) D = (const T*)a.D64 + base; else D = (const T*)a.D32 + base;
+  D = dmat<T>(a) + base;
   double* __restrict__ Jm = a.J + base;
   double* __restrict__ Km = a.K + base;
 

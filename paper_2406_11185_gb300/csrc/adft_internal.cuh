@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "adft.h"
+#include "adft_df.cuh"
 
 namespace adft {
 
@@ -19,6 +20,7 @@ constexpr int BOYS_MMAX = LTOT + 8;           // table columns
 constexpr double BOYS_H = 0.1;                // table spacing in T
 constexpr int BOYS_NT = 601;                  // T = 0 .. 60
 constexpr double BOYS_TMAX = 60.0;            // beyond: asymptotic / upward
+constexpr int BOYS_DF_NT = 961;               // double-float table: T = i/16, i < 961
 
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 __host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
@@ -57,6 +59,10 @@ struct BasisView {
   const float* boys32;
   const double* pp_o2p64;  // [npp]: 1 / (2p) of every primitive pair
   const float* pp_o2p32;
+  const PrimPair<df>* ppdf;  // double-float copies of the primitive pairs
+  const df* pp_o2pdf;
+  const df* boysdf;        // [BOYS_DF_NT][BOYS_MMAX+1] F_m(i/16) as double-float
+  const df* expdf;         // [BOYS_DF_NT] exp(-i/16)
   const double* pp_w64;    // [2][npp]: 2 a and 2 b of every primitive pair
   const float* pp_w32;
   long long npp;
@@ -91,6 +97,7 @@ struct JKLaunch {
   unsigned long long* counter;  // dynamic work counter (zeroed)
   const double* D64;        // Cartesian D [ncart][ncart]
   const float* D32;
+  const df* Ddf;
   double* J;                // Cartesian accumulators (unsymmetrised)
   double* K;
   const int* abort_flag;    // device flag polled between work chunks
@@ -105,6 +112,7 @@ struct GradLaunch {
 // Launchers implemented in the per-precision translation units.
 cudaError_t launch_jk_fp64(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
 cudaError_t launch_jk_fp32(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
+cudaError_t launch_jk_df(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
 cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
 cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
 cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s);
@@ -114,7 +122,7 @@ cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, co
 // basis creation (1e-3 of the paper's default tolerance 1e-12).
 constexpr double PRIM_EPS = 1e-15;
 // Boys tables in device memory of the current device (built once).
-cudaError_t boys_tables(const double** t64, const float** t32);
+cudaError_t boys_tables(const double** t64, const float** t32, const df** tdf, const df** edf);
 
 // Counted flops of one primitive quartet / one contracted quartet of a class
 // (used only for reporting).

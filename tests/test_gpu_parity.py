@@ -139,3 +139,27 @@ def test_abort_flag_reported():
     adft.adft_basis_set_abort(b, False)
     J, K = adft.adft_jk_build(b, Dt, thresh=opt["thresh"])
     assert adft.adft_jk_status(b) == 0
+
+
+@pytest.mark.parametrize("name,spherical", [("tiny", True), ("small", True), ("tiny_f", True), ("tiny_f", False)])
+def test_emulated_fp64_parity(name, spherical):
+    """Every quartet evaluated in double-float arithmetic (about 48 significant
+    bits): a precision level between FP32 and FP64, held to 1e-8 on J, K and E."""
+    mol, opt, D = _case(name, spherical)
+    Jr, Kr, Er = _oracle_jk(name, spherical, mol, D, opt["thresh"])
+    J, K, E, st, _ = _gpu_jk(mol, D, opt["thresh"], precision="emu")
+    dj, dk = np.max(np.abs(J - Jr)), np.max(np.abs(K - Kr))
+    print(f"emu {name} sph={spherical}: max|dJ|={dj:.2e} max|dK|={dk:.2e} |dE|={abs(E - Er):.2e}")
+    assert dj <= 1e-8 and dk <= 1e-8
+    assert abs(E - Er) <= 1e-8
+
+
+@pytest.mark.parametrize("name,split", [("tiny_f", 1e-5), ("small", 1e-5)])
+def test_mixed_emulated_energy(name, split):
+    mol, opt, D = _case(name)
+    Jr, Kr, Er = _oracle_jk(name, True, mol, D, opt["thresh"])
+    J, K, E, st, _ = _gpu_jk(mol, D, opt["thresh"], precision="mixed_emu", split=split)
+    print(f"mixed_emu {name} split={split}: |dE|={abs(E - Er):.2e} max|dJ|={np.max(np.abs(J - Jr)):.2e}")
+    assert st["quartets_fp32"] > 0
+    assert abs(E - Er) <= TOL_E_MIXED
+    assert np.max(np.abs(J - Jr)) <= 1e-5 and np.max(np.abs(K - Kr)) <= 1e-5
