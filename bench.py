@@ -9,11 +9,10 @@ timing, as in an SCF loop.  The metric is screened shell quartets per second
 of the mixed-precision build (--precision mixed: FP64 band in native FP64,
 FP32 band in FP32); the plain FP64 build of the same molecule is timed beside
 it, and the launch shape of every class-pair kernel is autotuned before
-timing.  --precision mixed_emu evaluates the FP64 band in double-float
-arithmetic instead (slower on this GPU in these kernels, kept for study).
+timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                  [--precision fp64|mixed|emu|mixed_emu] [--impl reference]
+                  [--precision fp64|mixed] [--impl reference]
 
 --impl reference times the CPU oracle (the plain FP64 reference written from
 the paper's definitions) on a bounded sample of the same workload.
@@ -44,6 +43,9 @@ WORKLOADS = {
            "516 spherical functions, thresh 1e-10, split 1e-5, mixed FP32/FP64",
     "small": "3 heavy (3s2p1d) + 5 H (2s1p) atoms, 1-6 primitives, exponents 0.1-5e3, "
              "67 spherical functions, thresh 1e-10, split 1e-5, mixed FP32/FP64 (profiling case)",
+    "batch256": "256 molecules of 10-40 atoms (40 % heavy, 3s2p1d / 2s1p, 1-6 primitives), 86-344 "
+                "spherical functions each; J, K, E and the nuclear gradient of every molecule in one "
+                "batched, graph-captured call per step; thresh 1e-10, split 1e-5, mixed FP32/FP64",
 }
 # Peaks of plain ALU arithmetic derived from unit counts and the maximum
 # clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz, and the FP64 rate of
@@ -51,8 +53,6 @@ WORKLOADS = {
 SMS, CLK_MAX = 152, 2.07e9
 PEAK_FP32 = SMS * 128 * 2 * CLK_MAX / 1e12
 PEAK_FP64 = SMS * 2 * 2 * CLK_MAX / 1e12
-# double-float FMA = 2 algorithmic flops for about 15 FP32 instructions
-PEAK_DF = PEAK_FP32 / 15
 
 
 def _dist():
@@ -152,6 +152,87 @@ def cpu_oracle_rate(mol, opt, D, budget_s=15.0, seed=7):
                       f"({kept} kept quartets in {dt:.2f} s, all host cores via OpenMP)"}
 
 
+def run_batch(args):
+    """The batched form: every molecule's J, K, E and gradient in one call
+    (one persistent kernel per class pair and band over all molecules,
+    replayed as a CUDA graph), against a loop of single-molecule calls of the
+    same kernels."""
+    import torch
+    from paper_2406_11185_gb300 import adft, parallel, synth
+    ws, rank, local = _dist()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    mols_all = synth.batch_molecules(256)
+    mine = parallel.shard_molecules(len(mols_all), rank, ws)
+    mols = [mols_all[i] for i in mine]
+    Ds = [synth.make_density(m, synth.default_nocc(m, None), 9000 + i) for i, m in zip(mine, mols)]
+    thresh, split = 1e-10, 1e-5
+    t0 = time.time()
+    bases = [adft.Basis.from_molecule(m) for m in mols]
+    bt = adft.Batch(bases)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    Dt = [torch.from_numpy(D).to(dev) for D in Ds]
+    Dp = bt.pack(Dt)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        t0 = time.time()
+        adft.adft_batch_autotune(bt, Dp, thresh=thresh, split=split, precision="mixed", stream=s)
+        tune_s = time.time() - t0
+        out = adft.adft_batch_jk(bt, Dp, thresh=thresh, split=split, precision="mixed", grad=True, stream=s)
+        for _ in range(args.warmup):
+            out = adft.adft_batch_jk(bt, Dp, thresh=thresh, split=split, precision="mixed", grad=True, stream=s,
+                                     out=out)
+        s.synchronize()
+        times = []
+        with ClockSampler(dev.index or 0) as clk:
+            for _ in range(args.steps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                out = adft.adft_batch_jk(bt, Dp, thresh=thresh, split=split, precision="mixed", grad=True,
+                                         stream=s, out=out)
+                b.record(s)
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+        st = adft.adft_batch_last_stats(bt)
+        # the same work as a loop of single-molecule calls (default launch shapes)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for bs, D in zip(bases, Dt):
+            adft.adft_jk_energy(bs, D, thresh=thresh, split=split, precision="mixed", check=False, stream=s,
+                                on_device=True)
+            adft.adft_jk_grad(bs, D, thresh=thresh, split=split, precision="mixed", check=False, stream=s)
+        b.record(s)
+        b.synchronize()
+        loop_ms = a.elapsed_time(b)
+    quartets = st["quartets_fp64"] + st["quartets_fp32"]
+    ms_total, all_q = parallel.aggregate(float(sum(times)), quartets * args.steps, device=dev)
+    ms = ms_total / args.steps
+    line = {"metric": METRIC, "value": all_q / (ms_total / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batch256: {WORKLOADS['batch256']}", "molecules_per_rank": len(mols),
+                       "nbf_total": int(sum(b.nbf for b in bases)), "precision": "mixed",
+                       "parallelism": f"molecules sharded x{ws}", "launch_shapes": "autotuned per class pair"},
+            "step": "J, K, E and gradient of every molecule, one graph replay",
+            "batched_s": ms / 1e3, "loop_of_single_calls_s": loop_ms / 1e3,
+            "speedup_vs_loop": loop_ms / ms, "setup_s": setup_s, "autotune_s": tune_s,
+            "quartets": {"fp64_band": st["quartets_fp64"], "fp32_band": st["quartets_fp32"]},
+            "clocks": clk.summary(),
+            # per step: D transform, screen, scan, J/K kernels per class pair and band,
+            # output transform, energy, gradient kernels per class pair and band
+            "gpu_launches": (5 + 4 * batch_class_pairs(mols)) * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def batch_class_pairs(mols):
+    ls = sorted({l for m in mols for _, l, _, _ in m.shells})
+    ncls = sum(1 for a in ls for b in ls if a >= b)
+    return ncls * (ncls + 1) // 2
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -182,10 +263,12 @@ def main():
     ap.add_argument("--impl", default="adft", choices=["adft", "reference"])
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "emu", "mixed_emu"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch256":
+        return run_batch(args)
 
     import torch
     ws, rank, local = _dist()
@@ -195,7 +278,7 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
-    from paper_2406_11185_gb300 import adft
+    from paper_2406_11185_gb300 import adft, parallel
 
     mol, opt, Dn = workload(args.workload)
     t0 = time.time()
@@ -230,9 +313,6 @@ def main():
     t0 = time.time()
     fp64_ms, E64, st64 = one_build("fp64")
     refs = {"fp64": {"s": fp64_ms / 1e3, "energy": E64}}
-    if prec not in ("mixed", "fp64"):
-        mms, Em, _ = one_build("mixed")
-        refs["mixed"] = {"s": mms / 1e3, "energy": Em, "err_vs_fp64": abs(Em - E64)}
     # autotune the timed precision (launch shape per class pair and band)
     tune = adft.adft_autotune(basis, D, thresh=thresh, split=split, precision=prec)
     tune_s = time.time() - t0
@@ -258,14 +338,11 @@ def main():
         torch.distributed.barrier()
     Emix = float(e.item())
     st = adft.adft_jk_last_stats(basis)
-    ms_total = float(sum(times))
-    if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms = ms_total / args.steps
     quartets = st["quartets_fp64"] + st["quartets_fp32"]
-    value = ws * quartets / (ms / 1e3)
+    # slowest rank's time, all ranks' work (replicas: each rank builds the molecule)
+    ms_total, all_quartets = parallel.aggregate(float(sum(times)), quartets * args.steps, device=dev)
+    ms = ms_total / args.steps
+    value = all_quartets / (ms_total / 1e3)
 
     # end to end through the C ABI with host buffers: pinned D in, J and K out
     Dh = torch.from_numpy(Dn).pin_memory()
@@ -289,11 +366,8 @@ def main():
 
     # roofline of the dominant kernel group (ALU-bound ERI kernels)
     ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
-    emu = prec in ("emu", "mixed_emu")
     groups = {"eri_fp32": (ph["eri_fp32_ms"], st["flops_fp32"], PEAK_FP32, "FP32 pipe"),
-              ("eri_fp64band_doublefloat" if emu else "eri_fp64"):
-                  (ph["eri_fp64_ms"], st["flops_fp64"], PEAK_DF if emu else PEAK_FP64,
-                   "FP32 pipe / 15 instructions per double-float FMA" if emu else "FP64 pipe")}
+              "eri_fp64": (ph["eri_fp64_ms"], st["flops_fp64"], PEAK_FP64, "FP64 pipe")}
     dom = max(groups, key=lambda k: groups[k][0])
     gms, gfl, gpk, gkind = groups[dom]
     ach = gfl / (gms / 1e3) / 1e12 if gms > 0 else 0.0
@@ -305,7 +379,7 @@ def main():
                       for k, v in groups.items()}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if not emu else "f32+f32x2(+f64 accumulate)",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "nbf": basis.nbf,
                        "natom": mol.natom, "nshell": mol.nshell, "thresh": thresh, "split": split,
@@ -323,7 +397,7 @@ def main():
             "e2e": {"value": ws * quartets / (np.mean(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
                     "d2h_bytes_per_step": 2 * nb2, "ms": float(np.mean(e2e_ms))},
             "gpu_launches": None, "roofline": roof}
-    line["gpu_launches"] = launches_per_step(basis_classes(mol), mixed=prec in ("mixed", "mixed_emu")) * args.steps
+    line["gpu_launches"] = launches_per_step(basis_classes(mol), mixed=prec == "mixed") * args.steps
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(mol, opt, Dn)
     if rank == 0:
