@@ -74,14 +74,10 @@ enum {
   ADFT_ERR_ABORTED = -8       /* the abort flag of the handle was raised */
 };
 
-/* Precision modes.  FP64: every kept quartet in native FP64.  MIXED: the
+/* Precision modes.  FP64: every kept quartet in FP64.  MIXED: the
  * Schwarz-bound dispatch of Sec. 1.2.2, FP64 iff Q_ab Q_cd >= split, else
- * FP32.  EMU and MIXED_EMU: the same, with the FP64 band evaluated in
- * double-float arithmetic (pairs of FP32 numbers, about 48 significant bits)
- * on the FP32 pipe, which on GB300 issues 64 times more FMAs than the FP64
- * pipe; accumulation into J and K stays FP64.  The gradient evaluates its
- * FP64 band in native FP64 in every mode. */
-enum { ADFT_PREC_FP64 = 0, ADFT_PREC_MIXED = 1, ADFT_PREC_EMU = 2, ADFT_PREC_MIXED_EMU = 3 };
+ * FP32 with its contributions added into FP64 accumulators. */
+enum { ADFT_PREC_FP64 = 0, ADFT_PREC_MIXED = 1 };
 
 typedef struct adft_basis adft_basis; /* opaque, library-owned */
 typedef struct adft_batch adft_batch; /* opaque, library-owned */
@@ -97,7 +93,7 @@ typedef struct {
 typedef struct {
   double thresh;   /* Schwarz threshold (>= 0): skip iff Q_ab Q_cd < thresh */
   double split;    /* mixed modes only: FP64 band iff Q_ab Q_cd >= split */
-  int precision;   /* ADFT_PREC_FP64, _MIXED, _EMU or _MIXED_EMU */
+  int precision;   /* ADFT_PREC_FP64 or ADFT_PREC_MIXED */
   int check;       /* 1: validate D on the device, synchronise the stream and
                       return ADFT_ERR_ASYM_D / ADFT_ERR_NONFINITE; 0: no check,
                       fully asynchronous */
@@ -170,11 +166,16 @@ int adft_jk_last_stats(adft_basis* b, adft_stats* st);
 int adft_jk_last_timings(adft_basis* b, double* ms);
 
 /* Autotuner (per angular-momentum class pair and precision band): times
- * every class-pair kernel of one build of D with 1, 2, 4 and 8 resident
- * blocks per SM and keeps the fastest launch shape in the handle for later
- * calls.  The J/K accumulators of the handle are left undefined.
+ * every class-pair kernel of one build of D in each kernel variant that
+ * serves the class pair (two for the classes with a d/p bra and a ket of at
+ * most 18 Cartesian components: a warp-per-quartet kernel and a cooperative
+ * group kernel; one elsewhere) and with 1, 2, 4 and 8 resident blocks per SM
+ * (counts that cannot be resident at once are skipped), and keeps the
+ * fastest choice in the handle for later calls.  The J/K accumulators of the
+ * handle are left undefined.
  *   table: host [2][55] ints (band-major: FP64 then FP32; class pair
- *   X(X+1)/2 + Y with class X = l_a(l_a+1)/2 + l_b) or NULL.
+ *   X(X+1)/2 + Y with class X = l_a(l_a+1)/2 + l_b) or NULL; each entry is
+ *   blocks_per_SM + 256 * variant.
  *   ms: host [2][55] doubles, the best time of every class-pair kernel
  *   (0 for empty ones), or NULL.
  * Synchronous. */
@@ -186,7 +187,9 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* opts, int* ta
  * quartets per band and class pair, or NULL.  Synchronous. */
 int adft_jk_plan(adft_basis* b, const double* D, const adft_opts* opts, adft_stats* st, int64_t* quartets);
 
-/* Install a launch-shape table (same layout as adft_autotune's). */
+/* Install a launch-shape table (same layout and encoding as adft_autotune's).
+ * ADFT_ERR_ARG if an entry's blocks per SM is outside 1..64 or its variant is
+ * not below the class pair's number of variants; the handle is unchanged then. */
 int adft_set_tuning(adft_basis* b, const int* table);
 
 /* Raise (1) or clear (0) the handle's abort flag.  A running or later build

@@ -25,8 +25,6 @@ ADFT_ERR_TIMEOUT = -7
 ADFT_ERR_ABORTED = -8
 ADFT_PREC_FP64 = 0
 ADFT_PREC_MIXED = 1
-ADFT_PREC_EMU = 2
-ADFT_PREC_MIXED_EMU = 3
 ADFT_LMAX = 3
 ADFT_MAX_NPRIM = 16
 ADFT_STATIC_MAX_NBF = 16384
@@ -130,8 +128,7 @@ def _stream_ptr(stream):
 
 
 def make_opts(thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None) -> adft_opts:
-    prec = {"fp64": ADFT_PREC_FP64, "mixed": ADFT_PREC_MIXED, "emu": ADFT_PREC_EMU,
-            "mixed_emu": ADFT_PREC_MIXED_EMU}[precision] if isinstance(precision, str) \
+    prec = {"fp64": ADFT_PREC_FP64, "mixed": ADFT_PREC_MIXED}[precision] if isinstance(precision, str) \
         else int(precision)
     return adft_opts(float(thresh), float(split), prec, 1 if check else 0, _stream_ptr(stream))
 
@@ -260,8 +257,9 @@ NCP = 55  # class pairs up to f shells
 def adft_autotune(basis: Basis, D, thresh=1e-12, split=1e-5, precision="mixed", stream=None,
                   return_times=False):
     """Run the launch-shape autotuner on density D; returns the [2, 55] table
-    of blocks per SM (FP64 band, FP32 band) now installed in the handle (and
-    the best kernel time of every class pair in ms with return_times)."""
+    (FP64 band, FP32 band) now installed in the handle, each entry
+    blocks_per_SM + TUNE_VARIANT_STRIDE * kernel_variant (and the best kernel
+    time of every class pair in ms with return_times)."""
     _check_matrix(D, basis.nbf)
     tab = (ctypes.c_int * (2 * NCP))()
     ms = (ctypes.c_double * (2 * NCP))()
@@ -283,7 +281,11 @@ def adft_jk_plan(basis: Basis, D, thresh=1e-12, split=1e-5, precision="mixed", s
     return {k: getattr(st, k) for k, _ in adft_stats._fields_}, np.array(q[:], dtype=np.int64).reshape(2, NCP)
 
 
+TUNE_VARIANT_STRIDE = 256
+
+
 def adft_set_tuning(basis: Basis, table) -> None:
+    """Install a [2, 55] launch-shape table (adft_autotune's encoding)."""
     t = np.ascontiguousarray(np.asarray(table, dtype=np.int32).reshape(-1))
     if t.size != 2 * NCP:
         raise ValueError("table must hold 2 x 55 entries")

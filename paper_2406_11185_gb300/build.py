@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 OUT = os.path.join(OUT_DIR, "libadft.so")
 SOURCES = ["adft_core.cu", "adft_dispatch.cu", "adft_grad.cu", "adft_static.cu"] + [
-    f"adft_eri{p}_{g}.cu" for p in ("64", "32", "df") for g in ("a", "b", "c", "d", "e", "f")]
+    f"adft_eri{p}_{g}.cu" for p in ("64", "32") for g in ("a", "b", "c", "d", "e", "f", "g", "h")] + [
+    f"adft_grad{p}_{g}.cu" for p in ("64", "32") for g in ("a", "b", "c")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -53,20 +53,7 @@ template <typename T, int L>
 __device__ __forceinline__ void prim_R_scaled(T alpha, T X, T Y, T Z, T pref, const BasisView& bv, T* R) {
   T B[L + 1];
   const T Tb = alpha * (X * X + Y * Y + Z * Z);
-  if constexpr (std::is_same<T, df>::value) {
-    boys_df_scaled<L>(Tb, bv, B);
-#pragma unroll
-    for (int n = 0; n <= L; ++n) B[n] *= (n & 1) ? -pref : pref;
-    const df sc = df_scale(alpha, Tb);
-    hermite_R_inplace<T, L>(B, X * sc, Y * sc, Z * sc, R);
-    df sp = sc;
-#pragma unroll
-    for (int n = 1; n <= L; ++n) {
-#pragma unroll
-      for (int x = nherm(n - 1); x < nherm(n); ++x) R[x] *= sp;
-      sp *= sc;
-    }
-  } else if constexpr (is_f64<T>) {
+  if constexpr (is_f64<T>) {
     boys_fp64<L>(Tb, bv.boys64, B);
     const T f = -2.0 * alpha;
     T pw = pref;
@@ -148,6 +135,28 @@ __device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket,
   }
 }
 
+// Group size: the number of lanes sharing one quartet.  It maximises the
+// useful fraction of the warp, (lanes in whole groups / 32) * (NCD / (GS * CK)),
+// with CK = ceil(NCD / GS) ket components per lane, under the register budget
+// NHAB * CK <= wmax for the per-lane W block and the shared-memory budget of
+// at least 4 warps per block (one per SM sub-partition).
+__host__ __device__ constexpr int coop_slots(int gs) { return gs < COOP_SLOT_CAP ? gs : COOP_SLOT_CAP; }
+__host__ __device__ constexpr int coop_group_size(int ncd, int nhab, int wmax, int nh, int ec, int nab, int ea,
+                                                  int tsize) {
+  int best = 32 < ncd ? 32 : ncd;
+  double best_u = -1.0;
+  for (int gs = 1; gs <= 32 && gs <= ncd; ++gs) {
+    const int ck = (ncd + gs - 1) / gs;
+    if (nhab * ck > wmax) continue;
+    const int group = coop_slots(gs) * (nh + 3 * ec) + nab * ncd + 3 * ea;
+    const int warp_bytes = (32 / gs) * group * tsize;
+    if (COOP_SMEM_BUDGET / warp_bytes < 4) continue;
+    const double u = (double)((32 / gs) * gs) / 32.0 * (double)ncd / (double)(gs * ck);
+    if (u > best_u + 1e-9) { best_u = u; best = gs; }
+  }
+  return best;
+}
+
 template <typename T, int LA, int LB, int LC, int LD>
 struct CoopPlan {
   static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
@@ -155,10 +164,11 @@ struct CoopPlan {
   static constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
   static constexpr int NHAB = nherm(LAB), NH = nherm(L);
   static constexpr int EA = (LA + 1) * (LB + 1) * (LAB + 1), EC = (LC + 1) * (LD + 1) * (LCD + 1);
-  static constexpr int GS = NCD < 32 ? NCD : 32;
+  static constexpr int WMAX = (sizeof(T) == 8 ? 80 : 100);
+  static constexpr int GS = coop_group_size(NCD, NHAB, WMAX, NH, EC, NAB, EA, (int)sizeof(T));
   static constexpr int CK = (NCD + GS - 1) / GS;
   static constexpr int NGW = 32 / GS;
-  static constexpr int SLOTS = GS < COOP_SLOT_CAP ? GS : COOP_SLOT_CAP;
+  static constexpr int SLOTS = coop_slots(GS);
   static constexpr int SLOT = NH + 3 * EC;
   static constexpr int GROUP = SLOTS * SLOT + NAB * NCD + 3 * EA;
   static constexpr int WARP_BYTES = NGW * GROUP * (int)sizeof(T);
@@ -167,7 +177,7 @@ struct CoopPlan {
   static constexpr int WREG = NHAB * CK;  // W values per lane (registers)
   // classes up to d shells (f classes keep the runtime-L kernel, which
   // compiles far faster)
-  static constexpr bool fits = WARPS >= 1 && WREG <= (sizeof(T) == 8 ? 80 : 160) && LA <= 2 && LC <= 2;
+  static constexpr bool fits = WARPS >= 1 && WREG <= WMAX && LA <= 2 && LC <= 2;
   static constexpr int SMEM = WARPS * WARP_BYTES;
 };
 
@@ -216,9 +226,9 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
     for (int ip = 0; ip < n0; ++ip) {
       const PrimPair<T> bp = pp[off0 + ip];
       const T o2p = __ldg(o2pa + off0 + ip);
-      if (gl < 3) {
-        const T PA = gl == 0 ? bp.PAx : gl == 1 ? bp.PAy : bp.PAz;
-        hermite_E<T, LA, LB>(PA, PA + AB[gl], o2p, Eab + gl * EA);
+      for (int d = gl; d < 3; d += GS) {  // groups may have fewer than 3 lanes
+        const T PA = d == 0 ? bp.PAx : d == 1 ? bp.PAy : bp.PAz;
+        hermite_E<T, LA, LB>(PA, PA + AB[d], o2p, Eab + d * EA);
       }
       T W[NHAB * CK];
 #pragma unroll

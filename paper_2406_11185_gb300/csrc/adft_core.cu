@@ -62,18 +62,11 @@ static void boys_row(double T, double* F) {
 struct DeviceTables {
   double* boys64 = nullptr;
   float* boys32 = nullptr;
-  df* boysdf = nullptr;
-  df* expdf = nullptr;
 };
-
-static df host_df(double x) {
-  const float h = (float)x;
-  return df(h, (float)(x - (double)h));
-}
 static std::mutex g_tab_mu;
 static DeviceTables g_tab[64];
 
-cudaError_t boys_tables(const double** t64, const float** t32, const df** tdf, const df** edf) {
+cudaError_t boys_tables(const double** t64, const float** t32) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -91,29 +84,11 @@ cudaError_t boys_tables(const double** t64, const float** t32, const df** tdf, c
     if ((e = cudaMalloc(&d32, hf.size() * sizeof(float))) != cudaSuccess) { cudaFree(d64); return e; }
     cudaMemcpy(d64, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(d32, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice);
-    // double-float tables at T = i/16
-    std::vector<double> row(W);
-    std::vector<df> hdf(BOYS_DF_NT * W), hex(BOYS_DF_NT);
-    for (int i = 0; i < BOYS_DF_NT; ++i) {
-      boys_row(i / 16.0, row.data());
-      for (int m = 0; m < W; ++m) hdf[i * W + m] = host_df(row[m]);
-      hex[i] = host_df((double)expl(-(long double)i / 16.0L));
-    }
-    df* ddf = nullptr;
-    df* dex = nullptr;
-    if ((e = cudaMalloc(&ddf, hdf.size() * sizeof(df))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&dex, hex.size() * sizeof(df))) != cudaSuccess) return e;
-    cudaMemcpy(ddf, hdf.data(), hdf.size() * sizeof(df), cudaMemcpyHostToDevice);
-    cudaMemcpy(dex, hex.data(), hex.size() * sizeof(df), cudaMemcpyHostToDevice);
     g_tab[dev].boys64 = d64;
     g_tab[dev].boys32 = d32;
-    g_tab[dev].boysdf = ddf;
-    g_tab[dev].expdf = dex;
   }
   *t64 = g_tab[dev].boys64;
   *t32 = g_tab[dev].boys32;
-  *tdf = g_tab[dev].boysdf;
-  *edf = g_tab[dev].expdf;
   return cudaSuccess;
 }
 
@@ -158,8 +133,7 @@ static void sph_coefficients(double out[LMAX + 1][2 * LMAX + 1][SPH_MAXC]) {
   }
 }
 
-static inline bool is_mixed(int prec) { return prec == ADFT_PREC_MIXED || prec == ADFT_PREC_MIXED_EMU; }
-static inline bool is_emulated(int prec) { return prec == ADFT_PREC_EMU || prec == ADFT_PREC_MIXED_EMU; }
+static inline bool is_mixed(int prec) { return prec == ADFT_PREC_MIXED; }
 
 // ---------------------------------------------------------------------------
 // basis handle
@@ -167,7 +141,6 @@ static inline bool is_emulated(int prec) { return prec == ADFT_PREC_EMU || prec 
 struct Workspace {
   double* Dc = nullptr;     // Cartesian D, packed per molecule
   float* Dc32 = nullptr;
-  df* Dcdf = nullptr;
   double* Jc = nullptr;     // Cartesian accumulators (unsymmetrised)
   double* Kc = nullptr;
   double* Jw = nullptr;     // J, K in the output basis (energy calls)
@@ -178,7 +151,7 @@ struct Workspace {
   int* kst32 = nullptr;     //                        first FP32 ket - class start
   long long* pre64 = nullptr;  // per class pair: prefix sums over its bras
   long long* pre32 = nullptr;
-  unsigned long long* counters = nullptr;  // [2 passes][2 * NCP] work counters
+  unsigned long long* counters = nullptr;  // [3 sets][2 * NCP] work counters
   int* status = nullptr;    // [4]: status word, abort flag
   double* scal = nullptr;   // [4]: energy, max|D|, max|D-D^T|
   double* Emol = nullptr;   // [nmol] energies
@@ -226,15 +199,12 @@ struct adft_basis {
   int *d_cfunc_shell = nullptr, *d_cfunc_comp = nullptr;  // Cartesian function -> (shell, component)
   const double* boys64 = nullptr;
   const float* boys32 = nullptr;
-  const adft::df* boysdf = nullptr;
-  const adft::df* expdf = nullptr;
-  adft::PrimPair<adft::df>* d_ppdf = nullptr;
-  adft::df* d_o2pdf = nullptr;
   adft::Workspace ws;
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int ev_valid = 0;
-  int tune_blocks[2][adft::NCP];  // blocks per SM of every class-pair kernel and band (autotuner)
+  int tune_blocks[2][adft::NCP];   // blocks per SM of every class-pair kernel and band (autotuner)
+  int tune_variant[2][adft::NCP];  // kernel variant of every class pair and band (autotuner)
   int sms = 152;
   std::vector<void*> allocations;
 };
@@ -280,7 +250,6 @@ static BasisView view(const adft_basis* b) {
   v.pp64 = b->d_pp64; v.pp32 = b->d_pp32; v.boys64 = b->boys64; v.boys32 = b->boys32;
   v.pp_w64 = b->d_ppw64; v.pp_w32 = b->d_ppw32; v.npp = b->npp;
   v.pp_o2p64 = b->d_o2p64; v.pp_o2p32 = b->d_o2p32;
-  v.ppdf = b->d_ppdf; v.pp_o2pdf = b->d_o2pdf; v.boysdf = b->boysdf; v.expdf = b->expdf;
   v.pair_mol = (b->nmol > 1) ? b->d_pair_mol : nullptr;
   v.mol_cbase = b->d_mol_cbase; v.mol_nc = b->d_mol_nc;
   return v;
@@ -294,7 +263,7 @@ __global__ void k_build_pairs(int npair, const int* __restrict__ pair_a, const i
                               const double* __restrict__ xyz, const double* __restrict__ exps,
                               const double* __restrict__ ncoefs, long long npp, PrimPair<double>* pp64,
                               PrimPair<float>* pp32, double* w64, float* w32, double* o2p64, float* o2p32,
-                              PrimPair<df>* ppdf, df* o2pdf, int* pp_pair) {
+                              int* pp_pair) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= npp) return;
   // pair owning primitive pair g (ppoff is ascending)
@@ -319,9 +288,6 @@ __global__ void k_build_pairs(int npair, const int* __restrict__ pair_a, const i
   w64[g] = 2.0 * a; w64[npp + g] = 2.0 * b;
   o2p64[g] = 0.5 / p;
   o2p32[g] = (float)(0.5 / p);
-  ppdf[g] = PrimPair<df>{to_df(Px), to_df(Py), to_df(Pz), to_df(p), to_df(Px - A[0]), to_df(Py - A[1]),
-                         to_df(Pz - A[2]), to_df(K)};
-  o2pdf[g] = to_df(0.5 / p);
   w32[g] = (float)(2.0 * a); w32[npp + g] = (float)(2.0 * b);
   if (pp_pair) pp_pair[g] = pr;
 }
@@ -545,8 +511,7 @@ __device__ __forceinline__ int find_mol(const long long* base, int nmol, long lo
   return lo;
 }
 
-__global__ void k_d_to_cart(XformArgs x, long long total, const double* __restrict__ D, double* Dc, float* Dc32,
-                            df* Dcdf) {
+__global__ void k_d_to_cart(XformArgs x, long long total, const double* __restrict__ D, double* Dc, float* Dc32) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int m = find_mol(x.cbase, x.nmol, g);
@@ -573,7 +538,6 @@ __global__ void k_d_to_cart(XformArgs x, long long total, const double* __restri
   }
   Dc[g] = v;
   Dc32[g] = (float)v;
-  Dcdf[g] = to_df(v);
 }
 
 __global__ void k_from_cart(XformArgs x, long long total, const double* __restrict__ Jc,
@@ -695,11 +659,11 @@ static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStrea
     k_check_d<<<(unsigned)((nb2 + T256 - 1) / T256), T256, 0, s>>>(x, nb2, D, w.scal, w.status);
     ADFT_CUDA(cudaGetLastError());
   }
-  k_d_to_cart<<<(unsigned)((nc2 + T256 - 1) / T256), T256, 0, s>>>(x, nc2, D, w.Dc, w.Dc32, w.Dcdf);
+  k_d_to_cart<<<(unsigned)((nc2 + T256 - 1) / T256), T256, 0, s>>>(x, nc2, D, w.Dc, w.Dc32);
   ADFT_CUDA(cudaGetLastError());
   ADFT_CUDA(cudaMemsetAsync(w.Jc, 0, nc2 * sizeof(double), s));
   ADFT_CUDA(cudaMemsetAsync(w.Kc, 0, nc2 * sizeof(double), s));
-  ADFT_CUDA(cudaMemsetAsync(w.counters, 0, 4 * NCP * sizeof(unsigned long long), s));
+  ADFT_CUDA(cudaMemsetAsync(w.counters, 0, 6 * NCP * sizeof(unsigned long long), s));
   ADFT_CUDA(cudaMemsetAsync(w.stats, 0, 8 * sizeof(unsigned long long), s));
 
   ScreenArgs sa;
@@ -743,7 +707,7 @@ static JKLaunch base_launch(adft_basis* b) {
   Workspace& w = b->ws;
   JKLaunch L;
   L.bv = view(b);
-  L.D64 = w.Dc; L.D32 = w.Dc32; L.Ddf = w.Dcdf; L.J = w.Jc; L.K = w.Kc;
+  L.D64 = w.Dc; L.D32 = w.Dc32; L.J = w.Jc; L.K = w.Kc;
   L.abort_flag = w.status + 1;
   L.status = w.status;
   return L;
@@ -768,7 +732,7 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
         L.ket_start = (band ? w.kst32 : w.kst64) + b->cnt_off[cp];
         L.counter = w.counters + 2 * NCP * pass + 2 * cp + band;
         const int grid = b->sms * b->tune_blocks[band][cp];
-        cudaError_t e = fn(X, Y, L, band, grid);
+        cudaError_t e = fn(X, Y, L, band, grid, b->tune_variant[band][cp]);
         if (e != cudaSuccess) {
           set_error(std::string(band ? "fp32" : "fp64") + " launch: " + cudaGetErrorString(e));
           return ADFT_ERR_CUDA;
@@ -783,19 +747,22 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
 static int run_jk(adft_basis* b, const double* D, const adft_opts* o, cudaStream_t s) {
   int st = prepare(b, D, o, s);
   if (st) return st;
-  return for_each_class_pair(b, o, base_launch(b), s, 0, [&](int X, int Y, const JKLaunch& L, int band, int grid) {
-    if (band == 1) return launch_jk_fp32(X, Y, L, grid, s);
-    return is_emulated(o->precision) ? launch_jk_df(X, Y, L, grid, s) : launch_jk_fp64(X, Y, L, grid, s);
+  return for_each_class_pair(b, o, base_launch(b), s, 0,
+                             [&](int X, int Y, const JKLaunch& L, int band, int grid, int variant) {
+    return band == 1 ? launch_jk_fp32(X, Y, L, grid, variant, s) : launch_jk_fp64(X, Y, L, grid, variant, s);
   });
 }
 
 static int run_grad(adft_basis* b, const adft_opts* o, cudaStream_t s, double* grad, int pass) {
   ADFT_CUDA(cudaMemsetAsync(grad, 0, 3 * sizeof(double) * b->natom, s));
-  return for_each_class_pair(b, o, base_launch(b), s, pass, [&](int X, int Y, const JKLaunch& L, int band, int grid) {
+  // counter sets: 0 J/K, 1 the first gradient pass after J/K in the same call
+  // (or the autotuner), 2 the second (swapped) gradient pass
+  return for_each_class_pair(b, o, base_launch(b), s, pass, [&](int X, int Y, const JKLaunch& L, int band, int, int) {
     GradLaunch g;
     g.jk = L;
     g.grad = grad;
-    return band == 0 ? launch_grad_fp64(X, Y, g, grid, s) : launch_grad_fp32(X, Y, g, grid, s);
+    g.counter2 = b->ws.counters + 4 * NCP + 2 * cp_index(X, Y) + band;
+    return band == 0 ? launch_grad_fp64(X, Y, g, b->sms, s) : launch_grad_fp32(X, Y, g, b->sms, s);
   });
 }
 
@@ -839,8 +806,8 @@ static int finish_check(adft_basis* b, const adft_opts* o, cudaStream_t s) {
 static int check_opts(const adft_opts* o) {
   if (!o) { set_error("opts is NULL"); return ADFT_ERR_ARG; }
   if (!(o->thresh >= 0.0) || !isfinite(o->thresh)) { set_error("thresh must be finite and >= 0"); return ADFT_ERR_ARG; }
-  if (o->precision < ADFT_PREC_FP64 || o->precision > ADFT_PREC_MIXED_EMU) {
-    set_error("precision must be ADFT_PREC_FP64, _MIXED, _EMU or _MIXED_EMU");
+  if (o->precision != ADFT_PREC_FP64 && o->precision != ADFT_PREC_MIXED) {
+    set_error("precision must be ADFT_PREC_FP64 or ADFT_PREC_MIXED");
     return ADFT_ERR_ARG;
   }
   if (is_mixed(o->precision) && (!(o->split >= 0.0) || !isfinite(o->split))) {
@@ -939,7 +906,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
   b->cls_first[NCLS] = (int)pa.size();
   b->npair = (int)pa.size();
 
-  st = boys_tables(&b->boys64, &b->boys32, &b->boysdf, &b->expdf);
+  st = boys_tables(&b->boys64, &b->boys32);
   if (st != cudaSuccess) { set_error("Boys table upload failed"); return ADFT_ERR_CUDA; }
   {
     double h_sph[LMAX + 1][2 * LMAX + 1][SPH_MAXC];
@@ -986,8 +953,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
           (r = dalloc(b, &b->d_pp64, (size_t)tot)) || (r = dalloc(b, &b->d_pp32, (size_t)tot)) ||
           (r = dalloc(b, &b->d_ppw64, 2 * (size_t)tot)) || (r = dalloc(b, &b->d_ppw32, 2 * (size_t)tot)) ||
           (r = dalloc(b, &b->d_pp_src, (size_t)tot)) || (r = dalloc(b, &b->d_o2p64, (size_t)tot)) ||
-          (r = dalloc(b, &b->d_o2p32, (size_t)tot)) || (r = dalloc(b, &b->d_ppdf, (size_t)tot)) ||
-          (r = dalloc(b, &b->d_o2pdf, (size_t)tot)))
+          (r = dalloc(b, &b->d_o2p32, (size_t)tot)))
         return r;
     }
     ADFT_CUDA(cudaMemcpy(b->d_pair_a, A.data(), A.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1006,7 +972,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
                                                          b->d_pp_src, b->d_shell_atom, b->d_shell_poff, b->d_xyz,
                                                          b->d_exps, b->d_ncoefs, tot, b->d_pp64, b->d_pp32,
                                                          b->d_ppw64, b->d_ppw32, b->d_o2p64, b->d_o2p32,
-                                                         b->d_ppdf, b->d_o2pdf, pp_pair_dev);
+                                                         pp_pair_dev);
       ADFT_CUDA(cudaGetLastError());
     }
     return ADFT_OK;
@@ -1080,16 +1046,16 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
         co += nX; po += nX + 1;
         b->tune_blocks[0][cp] = 4;
         b->tune_blocks[1][cp] = 8;
+        b->tune_variant[0][cp] = b->tune_variant[1][cp] = 0;
       }
     Workspace& w = b->ws;
     const size_t nc2 = (size_t)b->mol_cbase[b->nmol], nb2 = (size_t)b->mol_obase[b->nmol];
-    if ((st = dalloc(b, &w.Dc, nc2)) || (st = dalloc(b, &w.Dc32, nc2)) || (st = dalloc(b, &w.Dcdf, nc2)) ||
-        (st = dalloc(b, &w.Jc, nc2)) ||
+    if ((st = dalloc(b, &w.Dc, nc2)) || (st = dalloc(b, &w.Dc32, nc2)) || (st = dalloc(b, &w.Jc, nc2)) ||
         (st = dalloc(b, &w.Kc, nc2)) || (st = dalloc(b, &w.Jw, nb2)) || (st = dalloc(b, &w.Kw, nb2)) ||
         (st = dalloc(b, &w.cnt64, (size_t)co)) || (st = dalloc(b, &w.cnt32, (size_t)co)) ||
         (st = dalloc(b, &w.kst64, (size_t)co)) || (st = dalloc(b, &w.kst32, (size_t)co)) ||
         (st = dalloc(b, &w.pre64, (size_t)po)) || (st = dalloc(b, &w.pre32, (size_t)po)) ||
-        (st = dalloc(b, &w.counters, 4 * NCP)) || (st = dalloc(b, &w.status, 4)) ||
+        (st = dalloc(b, &w.counters, 6 * NCP)) || (st = dalloc(b, &w.status, 4)) ||
         (st = dalloc(b, &w.scal, 4)) || (st = dalloc(b, &w.Emol, (size_t)b->nmol)) || (st = dalloc(b, &w.stats, 8)))
       return st;
     ADFT_CUDA(cudaMemset(w.status, 0, 4 * sizeof(int)));
@@ -1300,7 +1266,22 @@ int adft_jk_status(adft_basis* b) {
   return st;
 }
 
-// ---- autotuner: blocks per SM of every class-pair kernel and band
+// ---- autotuner: kernel variant and blocks per SM of every class-pair kernel and band
+
+// table entry of the public tuning table: blocks per SM + TUNE_VARIANT_STRIDE * variant
+constexpr int TUNE_VARIANT_STRIDE = 256;
+
+static cudaError_t launch_band(int band, int X, int Y, const JKLaunch& L, int grid, int variant, cudaStream_t s,
+                               KernelInfo* info = nullptr) {
+  return band == 1 ? launch_jk_fp32(X, Y, L, grid, variant, s, info)
+                   : launch_jk_fp64(X, Y, L, grid, variant, s, info);
+}
+
+static void export_tuning(const adft_basis* b, int* table) {
+  for (int band = 0; band < 2; ++band)
+    for (int cp = 0; cp < NCP; ++cp)
+      table[band * NCP + cp] = b->tune_blocks[band][cp] + TUNE_VARIANT_STRIDE * b->tune_variant[band][cp];
+}
 
 int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table, double* ms_out) {
   int st = call_begin(b, D, o);
@@ -1318,33 +1299,39 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table
       for (int Y = X; Y >= 0; --Y) {
         const int cp = cp_index(X, Y);
         if (b->cls_first[X + 1] == b->cls_first[X] || b->cls_first[Y + 1] == b->cls_first[Y]) continue;
+        JKLaunch L = base_launch(b);
+        L.bra_first = b->cls_first[X]; L.nbra = b->cls_first[X + 1] - b->cls_first[X];
+        L.ket_first = b->cls_first[Y]; L.same_class = (X == Y);
+        L.prefix = (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp];
+        L.ket_start = (band ? b->ws.kst32 : b->ws.kst64) + b->cnt_off[cp];
+        L.counter = b->ws.counters + 2 * NCP + 2 * cp + band;
+        KernelInfo ki{1, 1};
+        ADFT_CUDA(launch_band(band, X, Y, L, 0, 0, s, &ki));
         float best = 1e30f;
-        int best_c = b->tune_blocks[band][cp];
-        for (int c : cand) {
-          JKLaunch L = base_launch(b);
-          L.bra_first = b->cls_first[X]; L.nbra = b->cls_first[X + 1] - b->cls_first[X];
-          L.ket_first = b->cls_first[Y]; L.same_class = (X == Y);
-          L.prefix = (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp];
-          L.ket_start = (band ? b->ws.kst32 : b->ws.kst64) + b->cnt_off[cp];
-          L.counter = b->ws.counters + 2 * NCP + 2 * cp + band;
-          ADFT_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s));
-          ADFT_CUDA(cudaEventRecord(e0, s));
-          cudaError_t e = band == 1 ? launch_jk_fp32(X, Y, L, b->sms * c, s)
-                          : is_emulated(o->precision) ? launch_jk_df(X, Y, L, b->sms * c, s)
-                                                      : launch_jk_fp64(X, Y, L, b->sms * c, s);
-          if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
-          ADFT_CUDA(cudaEventRecord(e1, s));
-          ADFT_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.0f;
-          ADFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-          if (ms < best * 0.97f) { best = ms; best_c = c; }
+        int best_c = b->tune_blocks[band][cp], best_v = b->tune_variant[band][cp];
+        for (int v = 0; v < ki.variants; ++v) {
+          KernelInfo kv{1, 1};
+          ADFT_CUDA(launch_band(band, X, Y, L, 0, v, s, &kv));
+          for (int c : cand) {
+            if (c > 1 && c > kv.max_blocks_per_sm) continue;  // would not be resident at once
+            ADFT_CUDA(cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), s));
+            ADFT_CUDA(cudaEventRecord(e0, s));
+            cudaError_t e = launch_band(band, X, Y, L, b->sms * c, v, s);
+            if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
+            ADFT_CUDA(cudaEventRecord(e1, s));
+            ADFT_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            ADFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best * 0.97f) { best = ms; best_c = c; best_v = v; }
+          }
         }
         b->tune_blocks[band][cp] = best_c;
+        b->tune_variant[band][cp] = best_v;
         if (ms_out) ms_out[band * NCP + cp] = best;
       }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (table) memcpy(table, b->tune_blocks, sizeof(b->tune_blocks));
+  if (table) export_tuning(b, table);
   return ADFT_OK;
 }
 
@@ -1371,9 +1358,24 @@ int adft_jk_plan(adft_basis* b, const double* D, const adft_opts* o, adft_stats*
 
 int adft_set_tuning(adft_basis* b, const int* table) {
   if (!b || !table) { set_error("NULL argument"); return ADFT_ERR_ARG; }
-  for (int i = 0; i < 2 * NCP; ++i)
-    if (table[i] < 1 || table[i] > 64) { set_error("blocks per SM must be in 1..64"); return ADFT_ERR_ARG; }
-  memcpy(b->tune_blocks, table, sizeof(b->tune_blocks));
+  for (int band = 0; band < 2; ++band)
+    for (int X = 0; X < NCLS; ++X)
+      for (int Y = 0; Y <= X; ++Y) {
+        const int cp = cp_index(X, Y), t = table[band * NCP + cp];
+        const int c = t % TUNE_VARIANT_STRIDE, v = t / TUNE_VARIANT_STRIDE;
+        KernelInfo ki{1, 1};
+        ADFT_CUDA(launch_band(band, X, Y, JKLaunch{}, 0, 0, nullptr, &ki));
+        if (t < 0 || c < 1 || c > 64 || v >= ki.variants) {
+          set_error("tuning entry " + std::to_string(band * NCP + cp) + ": blocks per SM must be in 1..64 and the "
+                    "variant below the class pair's variant count");
+          return ADFT_ERR_ARG;
+        }
+      }
+  for (int band = 0; band < 2; ++band)
+    for (int cp = 0; cp < NCP; ++cp) {
+      b->tune_blocks[band][cp] = table[band * NCP + cp] % TUNE_VARIANT_STRIDE;
+      b->tune_variant[band][cp] = table[band * NCP + cp] / TUNE_VARIANT_STRIDE;
+    }
   return ADFT_OK;
 }
 

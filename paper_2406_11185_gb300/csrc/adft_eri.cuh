@@ -54,13 +54,10 @@ template <typename T> __device__ __forceinline__ T dload(const T* p) { return __
 // constants and matrices of the three arithmetic types (double, float,
 // double-float)
 template <typename T> __device__ __forceinline__ constexpr T cst(double x) { return T(x); }
-template <> __device__ __forceinline__ constexpr df cst<df>(double x) { return dfc(x); }
 template <typename T> __device__ __forceinline__ const T* dmat(const JKLaunch& a);
 template <> __device__ __forceinline__ const double* dmat<double>(const JKLaunch& a) { return a.D64; }
 template <> __device__ __forceinline__ const float* dmat<float>(const JKLaunch& a) { return a.D32; }
-template <> __device__ __forceinline__ const df* dmat<df>(const JKLaunch& a) { return a.Ddf; }
 template <typename T> __device__ __forceinline__ T from_f64(double x) { return (T)x; }
-template <> __device__ __forceinline__ df from_f64<df>(double x) { return to_df(x); }
 template <typename T> constexpr bool is_f64 = std::is_same<T, double>::value;
 template <typename T> constexpr bool is_f32 = std::is_same<T, float>::value;
 
@@ -77,12 +74,6 @@ template <> struct Prec<double> {
   static __device__ __forceinline__ const PrimPair<double>* pp(const BasisView& b) { return b.pp64; }
   static __device__ __forceinline__ const double* o2p(const BasisView& b) { return b.pp_o2p64; }
   static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-  static constexpr int BUDGET = 640;
-};
-template <> struct Prec<df> {
-  static __device__ __forceinline__ const PrimPair<df>* pp(const BasisView& b) { return b.ppdf; }
-  static __device__ __forceinline__ const df* o2p(const BasisView& b) { return b.pp_o2pdf; }
-  static __device__ __forceinline__ df rsq(df x) { return rsqrt_df(x); }
   static constexpr int BUDGET = 640;
 };
 template <> struct Prec<float> {
@@ -160,85 +151,6 @@ __device__ __forceinline__ void boys_fp32_scaled(float T, const float* __restric
 #pragma unroll
     for (int m = 0; m < L; ++m) G[m + 1] = (2 * m + 1) * G[m];
   }
-}
-
-// Double-float, scaled like the FP32 version: G_m = c^m F_m(T), c = max(1, 2T).
-// Below T = 60: 7-term Taylor expansion of F_L about T_i = i/16 (|T - T_i| <=
-// 1/32), e^-T = e^-T_i e^(T_i - T) with an 8-term series, downward recursion;
-// above: G_0 = sqrt(pi/T)/2, G_{m+1} = (2m+1) G_m.
-__constant__ static const df c_inv_int_df[8] = {dfc(1.0), dfc(1.0), dfc(1.0 / 2), dfc(1.0 / 3),
-                                                dfc(1.0 / 4), dfc(1.0 / 5), dfc(1.0 / 6), dfc(1.0 / 7)};
-__constant__ static const df c_inv_fact_df[8] = {dfc(1.0), dfc(1.0), dfc(1.0 / 2), dfc(1.0 / 6),
-                                                 dfc(1.0 / 24), dfc(1.0 / 120), dfc(1.0 / 720), dfc(1.0 / 5040)};
-__constant__ static const df c_inv_odd_df[32] = {
-    dfc(1.0 / 1), dfc(1.0 / 3), dfc(1.0 / 5), dfc(1.0 / 7), dfc(1.0 / 9), dfc(1.0 / 11), dfc(1.0 / 13),
-    dfc(1.0 / 15), dfc(1.0 / 17), dfc(1.0 / 19), dfc(1.0 / 21), dfc(1.0 / 23), dfc(1.0 / 25), dfc(1.0 / 27),
-    dfc(1.0 / 29), dfc(1.0 / 31), dfc(1.0 / 33), dfc(1.0 / 35), dfc(1.0 / 37), dfc(1.0 / 39), dfc(1.0 / 41),
-    dfc(1.0 / 43), dfc(1.0 / 45), dfc(1.0 / 47), dfc(1.0 / 49), dfc(1.0 / 51), dfc(1.0 / 53), dfc(1.0 / 55),
-    dfc(1.0 / 57), dfc(1.0 / 59), dfc(1.0 / 61), dfc(1.0 / 63)};
-
-__device__ __forceinline__ df boys_df_lowT(int L, df T, const BasisView& bv, int& i_out, df& e_out) {
-  const int i = __float2int_rn(T.hi * 16.0f);
-  const df y = df((float)i * 0.0625f, 0.f) - T;
-  const df* row = bv.boysdf + i * (BOYS_MMAX + 1) + L;
-  df acc = __ldg(row + 6);
-#pragma unroll
-  for (int k = 6; k >= 1; --k) acc = __ldg(row + k - 1) + acc * (y * c_inv_int_df[k]);
-  df ey = c_inv_fact_df[7];
-#pragma unroll
-  for (int k = 6; k >= 0; --k) ey = c_inv_fact_df[k] + y * ey;
-  e_out = __ldg(bv.expdf + i) * ey;
-  i_out = i;
-  return acc;
-}
-
-template <int L>
-__device__ __forceinline__ void boys_df_scaled(df T, const BasisView& bv, df* G) {
-  if (T.hi < (float)BOYS_TMAX) {
-    int i;
-    df e;
-    G[L] = boys_df_lowT(L, T, bv, i, e);
-    const df T2 = df(2.0f * T.hi, 2.0f * T.lo);
-#pragma unroll
-    for (int m = L - 1; m >= 0; --m) G[m] = (T2 * G[m + 1] + e) * c_inv_odd_df[m];
-    if (T2.hi > 1.0f) {
-      df cn = T2;
-#pragma unroll
-      for (int m = 1; m <= L; ++m) { G[m] *= cn; cn *= T2; }
-    }
-  } else {
-    G[0] = dfc(0.88622692545275801365) * rsqrt_df(T);
-#pragma unroll
-    for (int m = 0; m < L; ++m) G[m + 1] = G[m] * df(2 * m + 1);
-  }
-}
-
-__device__ __forceinline__ void boys_df_scaled_rt(int L, df T, const BasisView& bv, df* G) {
-  if (T.hi < (float)BOYS_TMAX) {
-    int i;
-    df e;
-    G[L] = boys_df_lowT(L, T, bv, i, e);
-    const df T2 = df(2.0f * T.hi, 2.0f * T.lo);
-#pragma unroll 1
-    for (int m = L - 1; m >= 0; --m) G[m] = (T2 * G[m + 1] + e) * c_inv_odd_df[m];
-    if (T2.hi > 1.0f) {
-      df cn = T2;
-#pragma unroll 1
-      for (int m = 1; m <= L; ++m) { G[m] *= cn; cn *= T2; }
-    }
-  } else {
-    G[0] = dfc(0.88622692545275801365) * rsqrt_df(T);
-#pragma unroll 1
-    for (int m = 0; m < L; ++m) G[m + 1] = G[m] * df(2 * m + 1);
-  }
-}
-
-// scale factor s = sqrt(2 alpha / c), c = max(1, 2T), of the double-float
-// (and FP32) Hermite recursion
-__device__ __forceinline__ df df_scale(df alpha, df Tb) {
-  const df c = (2.0f * Tb.hi > 1.0f) ? df(2.0f * Tb.hi, 2.0f * Tb.lo) : df(1);
-  const df x = df(2.0f * alpha.hi, 2.0f * alpha.lo) * rcp_df(c);
-  return x * rsqrt_df(x);
 }
 
 // ---------------------------------------------------------------------------
@@ -322,20 +234,7 @@ template <typename T, int L>
 __device__ __forceinline__ void prim_R(T alpha, T X, T Y, T Z, const BasisView& bv, T* R) {
   T B[L + 1];
   const T Tb = alpha * (X * X + Y * Y + Z * Z);
-  if constexpr (std::is_same<T, df>::value) {
-    boys_df_scaled<L>(Tb, bv, B);
-#pragma unroll
-    for (int n = 1; n <= L; n += 2) B[n] = -B[n];
-    const df sc = df_scale(alpha, Tb);
-    hermite_R<T, L>(B, X * sc, Y * sc, Z * sc, R);
-    df sp = sc;
-#pragma unroll
-    for (int n = 1; n <= L; ++n) {
-#pragma unroll
-      for (int x = nherm(n - 1); x < nherm(n); ++x) R[x] *= sp;
-      sp *= sc;
-    }
-  } else if constexpr (is_f64<T>) {
+  if constexpr (is_f64<T>) {
     boys_fp64<L>(Tb, bv.boys64, B);
     T f = -2.0 * alpha, pw = f;
 #pragma unroll
@@ -600,20 +499,7 @@ template <typename T>
 __device__ __forceinline__ void prim_R_rt(int L, T alpha, T X, T Y, T Z, const BasisView& bv, T* R) {
   T B[GEN_L + 1];
   const T Tb = alpha * (X * X + Y * Y + Z * Z);
-  if constexpr (std::is_same<T, df>::value) {
-    boys_df_scaled_rt(L, Tb, bv, B);
-#pragma unroll 1
-    for (int n = 1; n <= L; n += 2) B[n] = -B[n];
-    const df sc = df_scale(alpha, Tb);
-    hermite_R_rt<T>(L, B, X * sc, Y * sc, Z * sc, R);
-    df sp = sc;
-#pragma unroll 1
-    for (int n = 1; n <= L; ++n) {
-      const int lo = n * (n + 1) * (n + 2) / 6, hi = (n + 1) * (n + 2) * (n + 3) / 6;
-      for (int x = lo; x < hi; ++x) R[x] *= sp;
-      sp *= sc;
-    }
-  } else if constexpr (is_f64<T>) {
+  if constexpr (is_f64<T>) {
     boys_fp64_rt(L, Tb, bv.boys64, B);
     const T f = -2.0 * alpha;
     T pw = f;
@@ -1045,36 +931,65 @@ static __global__ void __launch_bounds__(JK_THREADS) k_prim_schwarz(BasisView bv
 #endif  // ADFT_ERI_SCHWARZ
 
 #include "adft_coop.cuh"
+#include "adft_warp.cuh"
 
 // ---------------------------------------------------------------------------
 // dispatch: one launcher per (X, Y) class pair, X >= Y.  The launchers are
 // explicitly instantiated in several translation units (adft_eri_*.cu) so
 // that they compile in parallel; adft_dispatch.cu holds the tables.
 template <typename T, int X, int Y>
-cudaError_t launch_one(const JKLaunch& a, int grid, cudaStream_t s);
+cudaError_t launch_one(const JKLaunch& a, int grid, int variant, cudaStream_t s, KernelInfo* info);
 
 #ifndef ADFT_ERI_DECLARE_ONLY
+// Launch kern with smem bytes of dynamic shared memory, or, with info, report
+// how many blocks of it fit on one SM.  configured: the instantiation's
+// one-time flag for the shared-memory attribute.
+template <typename Kern>
+static cudaError_t start(Kern kern, const JKLaunch& a, int grid, int threads, int smem, bool& configured,
+                         int variants, cudaStream_t s, KernelInfo* info) {
+  if (smem > 0 && !configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (info) {
+    info->variants = variants;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&info->max_blocks_per_sm, kern, threads, smem);
+  }
+  kern<<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename T, int X, int Y>
-cudaError_t launch_one(const JKLaunch& a, int grid, cudaStream_t s) {
+cudaError_t launch_one(const JKLaunch& a, int grid, int variant, cudaStream_t s, KernelInfo* info) {
   constexpr int LA = cls_la(X), LB = cls_lb(X), LC = cls_la(Y), LD = cls_lb(Y);
   if constexpr (X < Y) {
     return cudaErrorInvalidValue;
   } else if constexpr (is_small_class(LA, LB, LC, LD)) {
-    k_jk<T, LA, LB, LC, LD><<<grid, JK_THREADS, 0, s>>>(a);
-  } else if constexpr (CoopPlan<T, LA, LB, LC, LD>::fits) {
-    using P = CoopPlan<T, LA, LB, LC, LD>;
-    static bool configured = false;  // one attribute call per instantiation
-    if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(k_jk_coop<T, LA, LB, LC, LD>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
-      if (e != cudaSuccess) return e;
-      configured = true;
+    static bool configured = false;
+    return start(k_jk<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured, 1, s, info);
+  } else if constexpr (WarpPlan<T, LA, LB, LC, LD>::fits) {
+    // Both kernels serve these classes and the autotuner picks one.  Variant 0
+    // is the warp kernel in FP64 and the cooperative one in FP32, the faster
+    // choice of each on the 60-atom workload.
+    static_assert(CoopPlan<T, LA, LB, LC, LD>::fits, "warp-kernel classes also need the cooperative kernel");
+    using W = WarpPlan<T, LA, LB, LC, LD>;
+    using C = CoopPlan<T, LA, LB, LC, LD>;
+    constexpr bool warp_first = sizeof(T) == 8;
+    if ((variant == 0) == warp_first) {
+      static bool configured = false;
+      return start(k_jk_warp<T, LA, LB, LC, LD>, a, grid, 32 * W::WARPS, W::SMEM, configured, 2, s, info);
     }
-    k_jk_coop<T, LA, LB, LC, LD><<<grid, 32 * P::WARPS, P::SMEM, s>>>(a);
+    static bool configured = false;
+    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured, 2, s, info);
+  } else if constexpr (CoopPlan<T, LA, LB, LC, LD>::fits) {
+    using C = CoopPlan<T, LA, LB, LC, LD>;
+    static bool configured = false;
+    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured, 1, s, info);
   } else {
-    k_jk_generic<T, LA, LB, LC, LD><<<grid, JK_THREADS, 0, s>>>(a);
+    static bool configured = false;
+    return start(k_jk_generic<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured, 1, s, info);
   }
-  return cudaGetLastError();
 }
 #endif
 

@@ -1,15 +1,12 @@
-// Class-pair ERI kernels (FP32 band), bra classes [5]: explicit
-// instantiations of the launchers of adft_eri.cuh, compiled in parallel with the
-// other groups.
+// Class-pair ERI kernels (FP32 band), class pairs [(5, 0), (5, 1), (5, 2)]:
+// explicit instantiations of the launchers of adft_eri.cuh, compiled in parallel
+// with the other groups.
 #include "adft_eri.cuh"
 
 namespace adft {
 
-template cudaError_t launch_one<float, 5, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<float, 5, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<float, 5, 2>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<float, 5, 3>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<float, 5, 4>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<float, 5, 5>(const JKLaunch&, int, cudaStream_t);
+template cudaError_t launch_one<float, 5, 0>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<float, 5, 1>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<float, 5, 2>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 
 }  // namespace adft

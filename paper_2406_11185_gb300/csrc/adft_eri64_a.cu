@@ -1,21 +1,21 @@
-// Class-pair ERI kernels (FP64 band), bra classes [9]: explicit
-// instantiations of the launchers of adft_eri.cuh, compiled in parallel with the
-// other groups; also the Schwarz-bound kernels.
+// Class-pair ERI kernels (FP64 band), class pairs [(9, 0), (9, 1), (9, 2), (9, 3), (9, 4), (9, 5), (9, 6), (9, 7), (9, 8), (9, 9)]:
+// explicit instantiations of the launchers of adft_eri.cuh, compiled in parallel
+// with the other groups; also the Schwarz-bound kernels.
 #define ADFT_ERI_SCHWARZ
 #include "adft_eri.cuh"
 
 namespace adft {
 
-template cudaError_t launch_one<double, 9, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 2>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 3>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 4>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 5>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 6>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 7>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 8>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 9, 9>(const JKLaunch&, int, cudaStream_t);
+template cudaError_t launch_one<double, 9, 0>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 1>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 2>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 3>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 4>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 5>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 6>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 7>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 8>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 9, 9>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 
 cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s) {
   if (X < 0 || X >= NCLS) return cudaErrorInvalidValue;

@@ -1,14 +1,12 @@
-// Class-pair ERI kernels (FP64 band), bra classes [4]: explicit
-// instantiations of the launchers of adft_eri.cuh, compiled in parallel with the
-// other groups.
+// Class-pair ERI kernels (FP64 band), class pairs [(5, 3), (5, 4), (5, 5)]:
+// explicit instantiations of the launchers of adft_eri.cuh, compiled in parallel
+// with the other groups.
 #include "adft_eri.cuh"
 
 namespace adft {
 
-template cudaError_t launch_one<double, 4, 0>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 1>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 2>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 3>(const JKLaunch&, int, cudaStream_t);
-template cudaError_t launch_one<double, 4, 4>(const JKLaunch&, int, cudaStream_t);
+template cudaError_t launch_one<double, 5, 3>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 5, 4>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
+template cudaError_t launch_one<double, 5, 5>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 
 }  // namespace adft

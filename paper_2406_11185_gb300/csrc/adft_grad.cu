@@ -1,4 +1,6 @@
-// Nuclear gradient of E_JK = 1/2 tr(DJ) - 1/4 tr(DK) at fixed D.
+// Nuclear gradient of E_JK = 1/2 tr(DJ) - 1/4 tr(DK) at fixed D: the launcher
+// tables, and the runtime-L kernel used for the class pairs that the
+// cooperative two-pass kernels of adft_gradk.cuh do not cover (f shells).
 //
 //   dE/dR = sum over unique shell quartets of n_img sum_block G_mnls d(mn|ls)/dR,
 //   G_mnls = 1/2 D_mn D_ls - 1/8 (D_ml D_ns + D_ms D_nl)
@@ -11,7 +13,9 @@
 // differentiated on the quartet (ab|cd), centre C on the swapped quartet
 // (cd|ab), and centre D follows from translational invariance
 // dD = -(dA + dB + dC).  Quartets are recomputed, none is stored.
+#define ADFT_ERI_DECLARE_ONLY
 #include "adft_eri.cuh"
+#include "adft_gradk.cuh"
 
 namespace adft {
 
@@ -123,19 +127,32 @@ __global__ void __launch_bounds__(JK_THREADS) k_grad_generic(GradLaunch g, int l
   }
 }
 
-static int grad_blocks(int dev_sms) { return dev_sms * 4; }
-
-cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s) {
+cudaError_t launch_grad_generic(bool fp64, int X, int Y, const GradLaunch& g, int sms, cudaStream_t s) {
   if (X < 0 || Y < 0 || X >= NCLS || Y > X) return cudaErrorInvalidValue;
-  (void)grad_blocks;
-  k_grad_generic<double><<<grid, JK_THREADS, 0, s>>>(a, cls_la(X), cls_lb(X), cls_la(Y), cls_lb(Y));
+  const int grid = sms * 4;
+  if (fp64)
+    k_grad_generic<double><<<grid, JK_THREADS, 0, s>>>(g, cls_la(X), cls_lb(X), cls_la(Y), cls_lb(Y));
+  else
+    k_grad_generic<float><<<grid, JK_THREADS, 0, s>>>(g, cls_la(X), cls_lb(X), cls_la(Y), cls_lb(Y));
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s) {
+template <typename T, int... I>
+static cudaError_t grad_dispatch(int X, int Y, const GradLaunch& g, int sms, cudaStream_t s,
+                                 std::integer_sequence<int, I...>) {
+  using Fn = cudaError_t (*)(const GradLaunch&, int, cudaStream_t);
+  // entries with Y > X are never called (guarded below); they point at a valid launcher
+  static constexpr Fn table[] = {&launch_grad_one<T, I / NCLS, (I % NCLS <= I / NCLS ? I % NCLS : 0)>...};
   if (X < 0 || Y < 0 || X >= NCLS || Y > X) return cudaErrorInvalidValue;
-  k_grad_generic<float><<<grid, JK_THREADS, 0, s>>>(a, cls_la(X), cls_lb(X), cls_la(Y), cls_lb(Y));
-  return cudaGetLastError();
+  return table[X * NCLS + Y](g, sms, s);
+}
+
+cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& g, int sms, cudaStream_t s) {
+  return grad_dispatch<double>(X, Y, g, sms, s, std::make_integer_sequence<int, NCLS * NCLS>{});
+}
+
+cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& g, int sms, cudaStream_t s) {
+  return grad_dispatch<float>(X, Y, g, sms, s, std::make_integer_sequence<int, NCLS * NCLS>{});
 }
 
 }  // namespace adft

@@ -8,7 +8,6 @@
 #include <vector>
 
 #include "adft.h"
-#include "adft_df.cuh"
 
 namespace adft {
 
@@ -20,7 +19,6 @@ constexpr int BOYS_MMAX = LTOT + 8;           // table columns
 constexpr double BOYS_H = 0.1;                // table spacing in T
 constexpr int BOYS_NT = 601;                  // T = 0 .. 60
 constexpr double BOYS_TMAX = 60.0;            // beyond: asymptotic / upward
-constexpr int BOYS_DF_NT = 961;               // double-float table: T = i/16, i < 961
 
 __host__ __device__ constexpr int ncart(int l) { return (l + 1) * (l + 2) / 2; }
 __host__ __device__ constexpr int nherm(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
@@ -59,10 +57,6 @@ struct BasisView {
   const float* boys32;
   const double* pp_o2p64;  // [npp]: 1 / (2p) of every primitive pair
   const float* pp_o2p32;
-  const PrimPair<df>* ppdf;  // double-float copies of the primitive pairs
-  const df* pp_o2pdf;
-  const df* boysdf;        // [BOYS_DF_NT][BOYS_MMAX+1] F_m(i/16) as double-float
-  const df* expdf;         // [BOYS_DF_NT] exp(-i/16)
   const double* pp_w64;    // [2][npp]: 2 a and 2 b of every primitive pair
   const float* pp_w32;
   long long npp;
@@ -97,7 +91,6 @@ struct JKLaunch {
   unsigned long long* counter;  // dynamic work counter (zeroed)
   const double* D64;        // Cartesian D [ncart][ncart]
   const float* D32;
-  const df* Ddf;
   double* J;                // Cartesian accumulators (unsymmetrised)
   double* K;
   const int* abort_flag;    // device flag polled between work chunks
@@ -106,15 +99,28 @@ struct JKLaunch {
 
 struct GradLaunch {
   JKLaunch jk;
-  double* grad;             // [natom][3]
+  double* grad;                    // [natom][3]
+  unsigned long long* counter2;    // work counter of the second (swapped) pass
 };
 
-// Launchers implemented in the per-precision translation units.
-cudaError_t launch_jk_fp64(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
-cudaError_t launch_jk_fp32(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
-cudaError_t launch_jk_df(int X, int Y, const JKLaunch& a, int grid, cudaStream_t s);
-cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
-cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& a, int grid, cudaStream_t s);
+// What a class-pair launcher reports instead of launching when asked: how many
+// kernel variants serve the class pair and how many blocks of the selected
+// variant fit on one SM.
+struct KernelInfo {
+  int variants;
+  int max_blocks_per_sm;
+};
+
+// Launchers implemented in the per-precision translation units.  variant
+// selects among the kernels that serve the class pair (0 = default); with
+// info != nullptr nothing is launched and *info is filled in.
+cudaError_t launch_jk_fp64(int X, int Y, const JKLaunch& a, int grid, int variant, cudaStream_t s,
+                           KernelInfo* info = nullptr);
+cudaError_t launch_jk_fp32(int X, int Y, const JKLaunch& a, int grid, int variant, cudaStream_t s,
+                           KernelInfo* info = nullptr);
+// Gradient launchers: the grid follows from the SM count and the kernel's occupancy.
+cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& a, int sms, cudaStream_t s);
+cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& a, int sms, cudaStream_t s);
 cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s);
 cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, const int* pp_pair, int npp_class,
                                 double* Qp, cudaStream_t s);
@@ -122,7 +128,7 @@ cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, co
 // basis creation (1e-3 of the paper's default tolerance 1e-12).
 constexpr double PRIM_EPS = 1e-15;
 // Boys tables in device memory of the current device (built once).
-cudaError_t boys_tables(const double** t64, const float** t32, const df** tdf, const df** edf);
+cudaError_t boys_tables(const double** t64, const float** t32);
 
 // Counted flops of one primitive quartet / one contracted quartet of a class
 // (used only for reporting).

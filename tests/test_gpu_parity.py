@@ -74,6 +74,35 @@ def test_mixed_precision_energy(name, split):
     assert dj <= 1e-5 and dk <= 1e-5
 
 
+# class pairs X(X+1)/2 + Y served by two kernels (warp per quartet and
+# cooperative group): (dp|pp), (dp|ds), (dp|dp)
+TWO_VARIANT_PAIRS = (12, 13, 14)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_alternative_kernel_variant_parity(precision):
+    mol, opt, D = _case("small")
+    Jr, Kr, Er = _oracle_jk("small", True, mol, D, opt["thresh"])
+    b = adft.Basis.from_molecule(mol)
+    tab = np.full((2, 55), 2, dtype=np.int32)
+    tab[:, list(TWO_VARIANT_PAIRS)] += adft.TUNE_VARIANT_STRIDE
+    adft.adft_set_tuning(b, tab)
+    bad = tab.copy()
+    bad[0, 0] += adft.TUNE_VARIANT_STRIDE  # (ss|ss) has one kernel only
+    with pytest.raises(adft.AdftError):
+        adft.adft_set_tuning(b, bad)
+    Dt = torch.from_numpy(D).cuda()
+    J, K = adft.adft_jk_build(b, Dt, thresh=opt["thresh"], precision=precision)
+    E = adft.adft_jk_energy(b, Dt, thresh=opt["thresh"], precision=precision)
+    dj = np.max(np.abs(J.cpu().numpy() - Jr))
+    dk = np.max(np.abs(K.cpu().numpy() - Kr))
+    print(f"variant 1 {precision}: max|dJ|={dj:.2e} max|dK|={dk:.2e} |dE|={abs(E - Er):.2e}")
+    if precision == "fp64":
+        assert dj <= TOL_JK and dk <= TOL_JK and abs(E - Er) <= TOL_E
+    else:
+        assert abs(E - Er) <= TOL_E_MIXED and dj <= 1e-5 and dk <= 1e-5
+
+
 def test_schwarz_bounds_match_oracle():
     mol, opt, D = _case("tiny_f")
     b = adft.Basis.from_molecule(mol)
@@ -140,26 +169,3 @@ def test_abort_flag_reported():
     J, K = adft.adft_jk_build(b, Dt, thresh=opt["thresh"])
     assert adft.adft_jk_status(b) == 0
 
-
-@pytest.mark.parametrize("name,spherical", [("tiny", True), ("small", True), ("tiny_f", True), ("tiny_f", False)])
-def test_emulated_fp64_parity(name, spherical):
-    """Every quartet evaluated in double-float arithmetic (about 48 significant
-    bits): a precision level between FP32 and FP64, held to 1e-8 on J, K and E."""
-    mol, opt, D = _case(name, spherical)
-    Jr, Kr, Er = _oracle_jk(name, spherical, mol, D, opt["thresh"])
-    J, K, E, st, _ = _gpu_jk(mol, D, opt["thresh"], precision="emu")
-    dj, dk = np.max(np.abs(J - Jr)), np.max(np.abs(K - Kr))
-    print(f"emu {name} sph={spherical}: max|dJ|={dj:.2e} max|dK|={dk:.2e} |dE|={abs(E - Er):.2e}")
-    assert dj <= 1e-8 and dk <= 1e-8
-    assert abs(E - Er) <= 1e-8
-
-
-@pytest.mark.parametrize("name,split", [("tiny_f", 1e-5), ("small", 1e-5)])
-def test_mixed_emulated_energy(name, split):
-    mol, opt, D = _case(name)
-    Jr, Kr, Er = _oracle_jk(name, True, mol, D, opt["thresh"])
-    J, K, E, st, _ = _gpu_jk(mol, D, opt["thresh"], precision="mixed_emu", split=split)
-    print(f"mixed_emu {name} split={split}: |dE|={abs(E - Er):.2e} max|dJ|={np.max(np.abs(J - Jr)):.2e}")
-    assert st["quartets_fp32"] > 0
-    assert abs(E - Er) <= TOL_E_MIXED
-    assert np.max(np.abs(J - Jr)) <= 1e-5 and np.max(np.abs(K - Kr)) <= 1e-5
