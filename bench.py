@@ -264,6 +264,8 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--grad", action="store_true",
+                    help="also time one nuclear gradient (adft_jk_grad) of the workload, outside the timed steps")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -398,6 +400,18 @@ def main():
                     "d2h_bytes_per_step": 2 * nb2, "ms": float(np.mean(e2e_ms))},
             "gpu_launches": None, "roofline": roof}
     line["gpu_launches"] = launches_per_step(basis_classes(mol), mixed=prec == "mixed") * args.steps
+    if args.grad:
+        # one gradient of E_JK at the same D and options (untimed by the step loop)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g = adft.adft_jk_grad(basis, D, thresh=thresh, split=split, precision=prec, check=False)
+        b.record(stream)
+        b.synchronize()
+        line["gradient"] = {"s": a.elapsed_time(b) / 1e3, "precision": prec,
+                            "max_abs": float(g.abs().max().item()),
+                            "net_force": float(g.sum(0).abs().max().item()),
+                            "phases_ms": adft.adft_jk_last_timings(basis)}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(mol, opt, Dn)
     if rank == 0:

@@ -167,9 +167,8 @@ int adft_jk_last_timings(adft_basis* b, double* ms);
 
 /* Autotuner (per angular-momentum class pair and precision band): times
  * every class-pair kernel of one build of D in each kernel variant that
- * serves the class pair (two for the classes with a d/p bra and a ket of at
- * most 18 Cartesian components: a warp-per-quartet kernel and a cooperative
- * group kernel; one elsewhere) and with 1, 2, 4 and 8 resident blocks per SM
+ * serves the class pair (two, a warp-per-quartet kernel and a cooperative
+ * group kernel, for (dp|pp), (dp|ds), (dp|dp); one elsewhere) and with 1, 2, 4 and 8 resident blocks per SM
  * (counts that cannot be resident at once are skipped), and keeps the
  * fastest choice in the handle for later calls.  The J/K accumulators of the
  * handle are left undefined.

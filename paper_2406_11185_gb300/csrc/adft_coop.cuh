@@ -18,6 +18,50 @@ constexpr int COOP_SLOT_CAP = 8;
 constexpr int COOP_SMEM_BUDGET = 200 * 1024;
 constexpr int COOP_MAX_WARPS = 8;
 
+// number of (tau, nu, phi) terms of the ket transform, summed over ket components
+template <int LC, int LD>
+__host__ __device__ constexpr int ket_terms() {
+  int n = 0;
+  for (int kc = 0; kc < ncart(LC) * ncart(LD); ++kc) {
+    const int ic = kc / ncart(LD), id = kc % ncart(LD);
+    n += (cart_pow(LC, ic, 0) + cart_pow(LD, id, 0) + 1) * (cart_pow(LC, ic, 1) + cart_pow(LD, id, 1) + 1) *
+         (cart_pow(LC, ic, 2) + cart_pow(LD, id, 2) + 1);
+  }
+  return n;
+}
+
+// Flat term list of the ket transform of class (LC, LD): the (tau, nu, phi)
+// triples of ket component kc, packed as tau | nu << 4 | phi << 8, are
+// terms[first[kc] .. first[kc + 1]).  A lane then runs one loop over its
+// component's terms, so the lanes of a group differ only in trip count (not
+// in the shape of three nested loops).  Built by thread 0 of the block.
+template <int LC, int LD>
+struct KetTermTable {
+  static constexpr int NCD = ncart(LC) * ncart(LD);
+  static constexpr int KT = ket_terms<LC, LD>();
+  unsigned short terms[KT];
+  unsigned short first[NCD + 1];
+};
+
+template <int LC, int LD>
+__device__ __forceinline__ void build_ket_terms(KetTermTable<LC, LD>& tab) {
+  constexpr int ND = ncart(LD), NCD = ncart(LC) * ND;
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int kc = 0; kc < NCD; ++kc) {
+      tab.first[kc] = (unsigned short)k;
+      const int ic = kc / ND, id = kc % ND;
+      const int sx = cart_x(LC, ic) + cart_x(LD, id), sy = cart_y(LC, ic) + cart_y(LD, id),
+                sz = cart_z(LC, ic) + cart_z(LD, id);
+      for (int tau = 0; tau <= sx; ++tau)
+        for (int nu = 0; nu <= sy; ++nu)
+          for (int phi = 0; phi <= sz; ++phi) tab.terms[k++] = (unsigned short)(tau | (nu << 4) | (phi << 8));
+    }
+    tab.first[NCD] = (unsigned short)k;
+  }
+  __syncthreads();
+}
+
 // In place Hermite integrals with compile-time L (same ordering argument as
 // hermite_R_rt: layer n overwrites layer n+1 by decreasing t+u+v).
 template <typename T, int L>
@@ -188,6 +232,8 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
   constexpr int NHAB = P::NHAB, NH = P::NH, EA = P::EA, EC = P::EC, LAB = P::LAB;
   constexpr int NTA = LAB + 1, NTC = P::LCD + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ KetTermTable<LC, LD> ktab;
+  build_ket_terms<LC, LD>(ktab);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / GS, gl = lane - g * GS;
   const bool in_group = g < P::NGW;
@@ -260,31 +306,31 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
               int cx, cy, cz, dx, dy, dz;
               cart_pows_rt(LC, kc / ND, cx, cy, cz);
               cart_pows_rt(LD, kc % ND, dx, dy, dz);
-              for (int tau = 0; tau <= cx + dx; ++tau) {
-                const T ex = Es[(cx * (LD + 1) + dx) * NTC + tau];
-                for (int nu = 0; nu <= cy + dy; ++nu) {
-                  const T exy = ex * Es[EC + (cy * (LD + 1) + dy) * NTC + nu];
-                  for (int phi = 0; phi <= cz + dz; ++phi) {
-                    T e2 = exy * Es[2 * EC + (cz * (LD + 1) + dz) * NTC + phi];
-                    if ((tau + nu + phi) & 1) e2 = -e2;
-                    // R index of (t+tau, u+nu, v+phi) = T3(n0 + sig) + T2(m0 + mu) + v + phi
-                    const int sig = tau + nu + phi, mu = nu + phi;
-                    int t3[LAB + 1], t2[LAB + 1];
+              const T* Ex = Es + (cx * (LD + 1) + dx) * NTC;
+              const T* Ey = Es + EC + (cy * (LD + 1) + dy) * NTC;
+              const T* Ez = Es + 2 * EC + (cz * (LD + 1) + dz) * NTC;
+              const int j1 = ktab.first[kc + 1];
+              for (int j = ktab.first[kc]; j < j1; ++j) {
+                const int pk = ktab.terms[j];
+                const int tau = pk & 15, nu = (pk >> 4) & 15, phi = pk >> 8;
+                T e2 = Ex[tau] * Ey[nu] * Ez[phi];
+                if ((tau + nu + phi) & 1) e2 = -e2;
+                // R index of (t+tau, u+nu, v+phi) = T3(n0 + sig) + T2(m0 + mu) + v + phi
+                const int sig = tau + nu + phi, mu = nu + phi;
+                int t3[LAB + 1], t2[LAB + 1];
 #pragma unroll
-                    for (int x = 0; x <= LAB; ++x) {
-                      const int nn = x + sig, mm = x + mu;
-                      t3[x] = nn * (nn + 1) * (nn + 2) / 6;
-                      t2[x] = mm * (mm + 1) / 2 + phi;
-                    }
-#pragma unroll
-                    for (int n = 0; n <= LAB; ++n)
-#pragma unroll
-                      for (int m = 0; m <= n; ++m)
-#pragma unroll
-                        for (int v = 0; v <= m; ++v)
-                          W[hidx(n - m, m - v, v) * CK + k] += e2 * Rs[t3[n] + t2[m] + v];
-                  }
+                for (int x = 0; x <= LAB; ++x) {
+                  const int nn = x + sig, mm = x + mu;
+                  t3[x] = nn * (nn + 1) * (nn + 2) / 6;
+                  t2[x] = mm * (mm + 1) / 2 + phi;
                 }
+#pragma unroll
+                for (int n = 0; n <= LAB; ++n)
+#pragma unroll
+                  for (int m = 0; m <= n; ++m)
+#pragma unroll
+                    for (int v = 0; v <= m; ++v)
+                      W[hidx(n - m, m - v, v) * CK + k] += e2 * Rs[t3[n] + t2[m] + v];
               }
             }
           }

@@ -992,6 +992,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
   {
     BasisView v = view(b);
     v.pair_mol = nullptr;  // bounds need no packed offsets
+    ADFT_CUDA(cudaMemset(b->d_pair_Q, 0, (size_t)b->npair * sizeof(double)));
     for (int X = 0; X < NCLS; ++X) {
       const int n = b->cls_first[X + 1] - b->cls_first[X];
       if (n == 0) continue;
@@ -1008,6 +1009,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
       set_error(std::string("schwarz readback: ") + cudaGetErrorString(cudaGetLastError()));
       return ADFT_ERR_CUDA;
     }
+    for (double& q : Q) q = sqrt(q);  // the kernel leaves max |(mn|mn)|
     const double qpmax = Qp.empty() ? 0.0 : *std::max_element(Qp.begin(), Qp.end());
     std::vector<int> idx(b->npair);
     std::iota(idx.begin(), idx.end(), 0);

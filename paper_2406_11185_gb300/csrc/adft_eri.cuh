@@ -887,23 +887,25 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
 }
 
 #ifdef ADFT_ERI_SCHWARZ
-// Schwarz bounds of the pairs of one class: Q = sqrt(max |(mn|mn)|), FP64.
+// Schwarz bounds of the pairs of one class, first step: max |(mn|mn)| over
+// the components of one chunk of one pair (one thread per (pair, chunk)),
+// combined with an integer atomicMax on the bits of the non-negative double
+// (its ordering matches); Qmax must be zero on entry and the caller takes
+// the square root.
 static __global__ void __launch_bounds__(JK_THREADS) k_schwarz_generic(BasisView bv, RtClass C, int first, int n,
-                                                                 double* Q) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int pr = first + i;
+                                                                 unsigned long long* Qmax) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * C.nchunk) return;
+  const int pr = first + (int)(t / C.nchunk), chunk = (int)(t % C.nchunk);
   const int NAB = ncart(C.la) * ncart(C.lb);
   double mx = 0.0;
   double G[GEN_BUDGET];
-  for (int chunk = 0; chunk < C.nchunk; ++chunk) {
-    quartet_block_rt<double>(C, bv, pr, pr, chunk, G);
-    for (int k = 0; k < C.ck; ++k) {
-      const int kc = chunk * C.ck + k;
-      if (kc < NAB) mx = fmax(mx, fabs(G[kc * C.ck + k]));
-    }
+  quartet_block_rt<double>(C, bv, pr, pr, chunk, G);
+  for (int k = 0; k < C.ck; ++k) {
+    const int kc = chunk * C.ck + k;
+    if (kc < NAB) mx = fmax(mx, fabs(G[kc * C.ck + k]));
   }
-  Q[pr] = sqrt(mx);
+  atomicMax(Qmax + pr, (unsigned long long)__double_as_longlong(mx));
 }
 
 // Primitive-pair bounds of the pairs of one class: Qp = sqrt(max |[mn|mn]_p|)

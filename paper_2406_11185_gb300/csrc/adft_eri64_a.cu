@@ -17,11 +17,13 @@ template cudaError_t launch_one<double, 9, 7>(const JKLaunch&, int, int, cudaStr
 template cudaError_t launch_one<double, 9, 8>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 template cudaError_t launch_one<double, 9, 9>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 
-cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Q, cudaStream_t s) {
+cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Qmax, cudaStream_t s) {
   if (X < 0 || X >= NCLS) return cudaErrorInvalidValue;
-  const int blocks = (n + JK_THREADS - 1) / JK_THREADS;
   const RtClass C = make_rt_class(cls_la(X), cls_lb(X), cls_la(X), cls_lb(X));
-  if (blocks > 0) k_schwarz_generic<<<blocks, JK_THREADS, 0, s>>>(bv, C, first, n, Q);
+  const long long threads = (long long)n * C.nchunk;
+  const int blocks = (int)((threads + JK_THREADS - 1) / JK_THREADS);
+  if (blocks > 0)
+    k_schwarz_generic<<<blocks, JK_THREADS, 0, s>>>(bv, C, first, n, reinterpret_cast<unsigned long long*>(Qmax));
   return cudaGetLastError();
 }
 

@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_grad_coop(GradLaunch gl
   constexpr int NT1 = P::NT1, NTC = P::LCD + 1, LB2 = LB + 2;
   const JKLaunch& a = gl_.jk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ KetTermTable<LC, LD> ktab;
+  build_ket_terms<LC, LD>(ktab);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / GS, gl = lane - g * GS;
   const bool in_group = g < P::NGW;
@@ -175,30 +177,30 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_grad_coop(GradLaunch gl
               int cx, cy, cz, dx, dy, dz;
               cart_pows_rt(LC, kc / ND, cx, cy, cz);
               cart_pows_rt(LD, kc % ND, dx, dy, dz);
-              for (int tau = 0; tau <= cx + dx; ++tau) {
-                const T ex = Es[(cx * (LD + 1) + dx) * NTC + tau];
-                for (int nu = 0; nu <= cy + dy; ++nu) {
-                  const T exy = ex * Es[EC + (cy * (LD + 1) + dy) * NTC + nu];
-                  for (int phi = 0; phi <= cz + dz; ++phi) {
-                    T e2 = exy * Es[2 * EC + (cz * (LD + 1) + dz) * NTC + phi];
-                    if ((tau + nu + phi) & 1) e2 = -e2;
-                    const int sig = tau + nu + phi, mu = nu + phi;
-                    int t3[LAB + 2], t2[LAB + 2];
+              const T* Ex = Es + (cx * (LD + 1) + dx) * NTC;
+              const T* Ey = Es + EC + (cy * (LD + 1) + dy) * NTC;
+              const T* Ez = Es + 2 * EC + (cz * (LD + 1) + dz) * NTC;
+              const int j1 = ktab.first[kc + 1];
+              for (int j = ktab.first[kc]; j < j1; ++j) {
+                const int pk = ktab.terms[j];
+                const int tau = pk & 15, nu = (pk >> 4) & 15, phi = pk >> 8;
+                T e2 = Ex[tau] * Ey[nu] * Ez[phi];
+                if ((tau + nu + phi) & 1) e2 = -e2;
+                const int sig = tau + nu + phi, mu = nu + phi;
+                int t3[LAB + 2], t2[LAB + 2];
 #pragma unroll
-                    for (int x = 0; x <= LAB + 1; ++x) {
-                      const int nn = x + sig, mm = x + mu;
-                      t3[x] = nn * (nn + 1) * (nn + 2) / 6;
-                      t2[x] = mm * (mm + 1) / 2 + phi;
-                    }
-#pragma unroll
-                    for (int nn = 0; nn <= LAB + 1; ++nn)
-#pragma unroll
-                      for (int m = 0; m <= nn; ++m)
-#pragma unroll
-                        for (int v = 0; v <= m; ++v)
-                          W[hidx(nn - m, m - v, v) * CK + k] += e2 * Rs[t3[nn] + t2[m] + v];
-                  }
+                for (int x = 0; x <= LAB + 1; ++x) {
+                  const int nn = x + sig, mm = x + mu;
+                  t3[x] = nn * (nn + 1) * (nn + 2) / 6;
+                  t2[x] = mm * (mm + 1) / 2 + phi;
                 }
+#pragma unroll
+                for (int nn = 0; nn <= LAB + 1; ++nn)
+#pragma unroll
+                  for (int m = 0; m <= nn; ++m)
+#pragma unroll
+                    for (int v = 0; v <= m; ++v)
+                      W[hidx(nn - m, m - v, v) * CK + k] += e2 * Rs[t3[nn] + t2[m] + v];
               }
             }
           }

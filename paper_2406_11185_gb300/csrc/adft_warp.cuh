@@ -18,18 +18,6 @@
 #pragma once
 // (included by adft_eri.cuh inside namespace adft)
 
-// number of (tau, nu, phi) terms of the ket transform, summed over ket components
-template <int LC, int LD>
-__host__ __device__ constexpr int ket_terms() {
-  int n = 0;
-  for (int kc = 0; kc < ncart(LC) * ncart(LD); ++kc) {
-    const int ic = kc / ncart(LD), id = kc % ncart(LD);
-    n += (cart_pow(LC, ic, 0) + cart_pow(LD, id, 0) + 1) * (cart_pow(LC, ic, 1) + cart_pow(LD, id, 1) + 1) *
-         (cart_pow(LC, ic, 2) + cart_pow(LD, id, 2) + 1);
-  }
-  return n;
-}
-
 // (ia, ib, t, u, v) of the k-th bra term in the order of the bra transform
 // (integer work only, done once per entry and bra primitive)
 template <int LA, int LB>
@@ -76,8 +64,11 @@ struct WarpPlan {
   static constexpr int WFIT = COOP_SMEM_BUDGET / WARP_BYTES;
   static constexpr int WARPS = WFIT > COOP_MAX_WARPS ? COOP_MAX_WARPS : WFIT;
   static constexpr int SMEM = WARPS * WARP_BYTES;
-  // bra with at most 32 Hermite functions and at most 18 ket components (larger
-  // unrolled bodies compile too slowly); the other d classes use k_jk_coop
+  // bra with at most 32 Hermite functions (one per lane) and at most 18 ket
+  // components.  Larger unrolled bodies spill and compile too slowly, and for
+  // d/d bras (two Hermite passes per lane, 35 of 64 lane slots busy) the
+  // cooperative kernel was faster on every class measured; those classes use
+  // k_jk_coop only.
   static constexpr bool fits = WARPS >= 2 && HP == 1 && NCD <= 18 && LA <= 2 && LC <= 2;
 };
 
