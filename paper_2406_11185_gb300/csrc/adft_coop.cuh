@@ -246,6 +246,9 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
   const BasisView& bv = a.bv;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
   const T* __restrict__ o2pa = Prec<T>::o2p(bv);
+  const float* __restrict__ qa = bv.pp_q32;
+  const float eps = (float)a.prim_eps;
+  unsigned cpq = 0, cbp = 0;  // evaluated work (group leaders)
 
   for (;;) {
     unsigned long long base = 0;
@@ -269,7 +272,11 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
     for (int kc = gl; kc < NCD; kc += GS)
       for (int ab = 0; ab < NAB; ++ab) Gs[ab * NCD + kc] = T(0);
 
+    int n1e = n1;
     for (int ip = 0; ip < n0; ++ip) {
+      n1e = shrink_kept(qa + off1, __ldg(qa + off0 + ip), eps, n1e);  // same in every lane
+      if (n1e == 0) break;
+      if (gl == 0) { cpq += n1e; ++cbp; }
       const PrimPair<T> bp = pp[off0 + ip];
       const T o2p = __ldg(o2pa + off0 + ip);
       for (int d = gl; d < 3; d += GS) {  // groups may have fewer than 3 lanes
@@ -280,8 +287,8 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
 #pragma unroll
       for (int x = 0; x < NHAB * CK; ++x) W[x] = T(0);
       __syncwarp(gmask);
-      for (int q0 = 0; q0 < n1; q0 += P::SLOTS) {
-        const int nv = min(P::SLOTS, n1 - q0);
+      for (int q0 = 0; q0 < n1e; q0 += P::SLOTS) {
+        const int nv = min(P::SLOTS, n1e - q0);
         if (gl < nv) {
           const int iq = off1 + q0 + gl;
           const PrimPair<T> kq = pp[iq];
@@ -366,4 +373,5 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
     digest_coop<T, LA, LB, LC, LD>(a, bra, ket, gl, GS, Gs);
     __syncwarp(gmask);
   }
+  flush_work(a.work, cpq, cbp);
 }

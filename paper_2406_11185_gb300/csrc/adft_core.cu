@@ -155,7 +155,8 @@ struct Workspace {
   int* status = nullptr;    // [4]: status word, abort flag
   double* scal = nullptr;   // [4]: energy, max|D|, max|D-D^T|
   double* Emol = nullptr;   // [nmol] energies
-  unsigned long long* stats = nullptr;     // [8]
+  unsigned long long* stats = nullptr;     // [10], see ScreenArgs::stats
+  unsigned long long* work = nullptr;      // [2 bands][NCP][2] evaluated primitive quartets, bra primitives
 };
 
 }  // namespace adft
@@ -194,6 +195,8 @@ struct adft_basis {
   double* d_ppw64 = nullptr;  // [2][npp] 2a, 2b
   double* d_o2p64 = nullptr;  // [npp] 1/(2p)
   float* d_o2p32 = nullptr;
+  float* d_ppq32 = nullptr;   // [npp] primitive-pair bound Q_p, descending within each pair
+  bool work_valid = false;    // the last call ran the J/K kernels (evaluated-work counters filled)
   float* d_ppw32 = nullptr;
   int *d_func_shell = nullptr, *d_func_comp = nullptr;    // output function -> (shell, component)
   int *d_cfunc_shell = nullptr, *d_cfunc_comp = nullptr;  // Cartesian function -> (shell, component)
@@ -250,6 +253,7 @@ static BasisView view(const adft_basis* b) {
   v.pp64 = b->d_pp64; v.pp32 = b->d_pp32; v.boys64 = b->boys64; v.boys32 = b->boys32;
   v.pp_w64 = b->d_ppw64; v.pp_w32 = b->d_ppw32; v.npp = b->npp;
   v.pp_o2p64 = b->d_o2p64; v.pp_o2p32 = b->d_o2p32;
+  v.pp_q32 = b->d_ppq32;
   v.pair_mol = (b->nmol > 1) ? b->d_pair_mol : nullptr;
   v.mol_cbase = b->d_mol_cbase; v.mol_nc = b->d_mol_nc;
   return v;
@@ -312,7 +316,10 @@ struct ScreenArgs {
   int* cnt32;
   int* kst64;
   int* kst32;
-  unsigned long long* stats;  // [0] q64 [1] q32 [2] total unique [3] prim64 [4] prim32 [5] flop64 [6] flop32
+  // [0] q64 [1] q32 [2] total unique [3] prim64 [4] prim32 [5] flop64 [6] flop32 (primitive
+  // counts and flops before primitive-quartet screening) [7] flop64 [8] flop32 of the
+  // per-quartet part only (the kernels count the primitive-level part)
+  unsigned long long* stats;
   float f_pq[NCP], f_bra[NCP], f_q[NCP];
 };
 
@@ -329,7 +336,7 @@ __device__ __forceinline__ int count_prefix(const double* Q, int first, int n, d
 __global__ void k_screen(ScreenArgs a, int npair) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long q64 = 0, q32 = 0, tot = 0, p64 = 0, p32 = 0;
-  double f64 = 0.0, f32 = 0.0;
+  double f64 = 0.0, f32 = 0.0, g64 = 0.0, g32 = 0.0;
   if (i < npair) {
     int X = 0;
     while (a.cls_first[X + 1] <= i) ++X;
@@ -357,6 +364,8 @@ __global__ void k_screen(ScreenArgs a, int npair) {
       p64 += s64 * nppi; p32 += s32 * nppi;
       f64 += (double)a.f_pq[cp] * nppi * s64 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * n64;
       f32 += (double)a.f_pq[cp] * nppi * s32 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * (keep - n64);
+      g64 += (double)a.f_q[cp] * n64;
+      g32 += (double)a.f_q[cp] * (keep - n64);
     }
   }
   // warp-reduce the statistics, one atomic per warp
@@ -368,11 +377,14 @@ __global__ void k_screen(ScreenArgs a, int npair) {
     p32 += __shfl_down_sync(0xffffffffu, p32, o);
     f64 += __shfl_down_sync(0xffffffffu, f64, o);
     f32 += __shfl_down_sync(0xffffffffu, f32, o);
+    g64 += __shfl_down_sync(0xffffffffu, g64, o);
+    g32 += __shfl_down_sync(0xffffffffu, g32, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(a.stats + 0, q64); atomicAdd(a.stats + 1, q32); atomicAdd(a.stats + 2, tot);
     atomicAdd(a.stats + 3, p64); atomicAdd(a.stats + 4, p32);
     atomicAdd(a.stats + 5, (unsigned long long)f64); atomicAdd(a.stats + 6, (unsigned long long)f32);
+    atomicAdd(a.stats + 7, (unsigned long long)g64); atomicAdd(a.stats + 8, (unsigned long long)g32);
   }
 }
 
@@ -664,7 +676,9 @@ static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStrea
   ADFT_CUDA(cudaMemsetAsync(w.Jc, 0, nc2 * sizeof(double), s));
   ADFT_CUDA(cudaMemsetAsync(w.Kc, 0, nc2 * sizeof(double), s));
   ADFT_CUDA(cudaMemsetAsync(w.counters, 0, 6 * NCP * sizeof(unsigned long long), s));
-  ADFT_CUDA(cudaMemsetAsync(w.stats, 0, 8 * sizeof(unsigned long long), s));
+  ADFT_CUDA(cudaMemsetAsync(w.stats, 0, 10 * sizeof(unsigned long long), s));
+  ADFT_CUDA(cudaMemsetAsync(w.work, 0, 4 * NCP * sizeof(unsigned long long), s));
+  b->work_valid = false;
 
   ScreenArgs sa;
   memcpy(sa.cls_first, b->cls_first, sizeof(sa.cls_first));
@@ -710,6 +724,8 @@ static JKLaunch base_launch(adft_basis* b) {
   L.D64 = w.Dc; L.D32 = w.Dc32; L.J = w.Jc; L.K = w.Kc;
   L.abort_flag = w.status + 1;
   L.status = w.status;
+  L.prim_eps = 0.0;
+  L.work = nullptr;
   return L;
 }
 
@@ -731,6 +747,8 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
         L.prefix = (band ? w.pre32 : w.pre64) + b->pre_off[cp];
         L.ket_start = (band ? w.kst32 : w.kst64) + b->cnt_off[cp];
         L.counter = w.counters + 2 * NCP * pass + 2 * cp + band;
+        L.prim_eps = PRIM_QUARTET_FRAC * o->thresh;
+        L.work = w.work + 2 * (band * NCP + cp);
         const int grid = b->sms * b->tune_blocks[band][cp];
         cudaError_t e = fn(X, Y, L, band, grid, b->tune_variant[band][cp]);
         if (e != cudaSuccess) {
@@ -747,6 +765,7 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
 static int run_jk(adft_basis* b, const double* D, const adft_opts* o, cudaStream_t s) {
   int st = prepare(b, D, o, s);
   if (st) return st;
+  b->work_valid = true;
   return for_each_class_pair(b, o, base_launch(b), s, 0,
                              [&](int X, int Y, const JKLaunch& L, int band, int grid, int variant) {
     return band == 1 ? launch_jk_fp32(X, Y, L, grid, variant, s) : launch_jk_fp64(X, Y, L, grid, variant, s);
@@ -1019,18 +1038,30 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
                          idx.begin() + b->seg_first[X * (b->nmol + 1) + m + 1],
                          [&](int i, int j) { return Q[i] > Q[j]; });
     std::vector<int> sa(b->npair), sb(b->npair), nsrc, nppoff(b->npair), nppn(b->npair);
+    std::vector<double> nqp;  // bound of every kept primitive pair, in the new order
     b->pair_Q.resize(b->npair);
     b->npp_dense = (long long)src.size();
     for (int i = 0; i < b->npair; ++i) {
       const int o = idx[i];
       sa[i] = pa[o]; sb[i] = pb[o]; b->pair_Q[i] = Q[o];
       nppoff[i] = (int)nsrc.size();
+      // kept primitive pairs by descending bound, so that the primitive
+      // quartets kept by the kernels' screening are a prefix of the ket's
+      std::vector<std::pair<double, int>> kp;
       for (int k = ppoff[o]; k < ppoff[o] + ppn[o]; ++k)
-        if (Qp[k] * qpmax > PRIM_EPS) nsrc.push_back(src[k]);
+        if (Qp[k] * qpmax > PRIM_EPS) kp.emplace_back(Qp[k], src[k]);
+      std::stable_sort(kp.begin(), kp.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first;
+      });
+      for (const auto& e : kp) { nsrc.push_back(e.second); nqp.push_back(e.first); }
       nppn[i] = (int)nsrc.size() - nppoff[i];
     }
     b->pair_a = sa; b->pair_b = sb;
     if ((st = build(sa, sb, nsrc, nppoff, nppn, false, nullptr))) return st;
+    {
+      std::vector<float> nqp32(nqp.begin(), nqp.end());
+      if ((st = upload(b, &b->d_ppq32, nqp32))) return st;
+    }
     ADFT_CUDA(cudaMemcpy(b->d_pair_Q, b->pair_Q.data(), b->npair * sizeof(double), cudaMemcpyHostToDevice));
     std::vector<long long> cum(b->npair + 1, 0);
     for (int i = 0; i < b->npair; ++i) cum[i + 1] = cum[i] + nppn[i];
@@ -1058,7 +1089,8 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
         (st = dalloc(b, &w.kst64, (size_t)co)) || (st = dalloc(b, &w.kst32, (size_t)co)) ||
         (st = dalloc(b, &w.pre64, (size_t)po)) || (st = dalloc(b, &w.pre32, (size_t)po)) ||
         (st = dalloc(b, &w.counters, 6 * NCP)) || (st = dalloc(b, &w.status, 4)) ||
-        (st = dalloc(b, &w.scal, 4)) || (st = dalloc(b, &w.Emol, (size_t)b->nmol)) || (st = dalloc(b, &w.stats, 8)))
+        (st = dalloc(b, &w.scal, 4)) || (st = dalloc(b, &w.Emol, (size_t)b->nmol)) || (st = dalloc(b, &w.stats, 10)) ||
+        (st = dalloc(b, &w.work, 4 * NCP)))
       return st;
     ADFT_CUDA(cudaMemset(w.status, 0, 4 * sizeof(int)));
   }
@@ -1228,7 +1260,7 @@ int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* o, double* gra
 
 int adft_jk_last_stats(adft_basis* b, adft_stats* out) {
   if (!b || !out) { set_error("NULL argument"); return ADFT_ERR_ARG; }
-  unsigned long long h[8];
+  unsigned long long h[10];
   ADFT_CUDA(cudaStreamSynchronize(b->last_stream));
   ADFT_CUDA(cudaMemcpy(h, b->ws.stats, sizeof(h), cudaMemcpyDeviceToHost));
   out->quartets_fp64 = (int64_t)h[0];
@@ -1238,6 +1270,25 @@ int adft_jk_last_stats(adft_basis* b, adft_stats* out) {
   out->prim_quartets_fp32 = (int64_t)h[4];
   out->flops_fp64 = (double)h[5];
   out->flops_fp32 = (double)h[6];
+  if (b->work_valid) {  // what the kernels evaluated after primitive-quartet screening
+    std::vector<unsigned long long> wk(4 * NCP);
+    ADFT_CUDA(cudaMemcpy(wk.data(), b->ws.work, wk.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    double fl[2] = {(double)h[7], (double)h[8]};
+    unsigned long long pq[2] = {0, 0};
+    for (int band = 0; band < 2; ++band)
+      for (int X = 0; X < NCLS; ++X)
+        for (int Y = 0; Y <= X; ++Y) {
+          const int cp = cp_index(X, Y);
+          const ClassFlops f = class_flops(cls_la(X), cls_lb(X), cls_la(Y), cls_lb(Y));
+          const unsigned long long* c = wk.data() + 2 * (band * NCP + cp);
+          pq[band] += c[0];
+          fl[band] += f.per_pq * (double)c[0] + f.per_bra * (double)c[1];
+        }
+    out->prim_quartets_fp64 = (int64_t)pq[0];
+    out->prim_quartets_fp32 = (int64_t)pq[1];
+    out->flops_fp64 = fl[0];
+    out->flops_fp32 = fl[1];
+  }
   return ADFT_OK;
 }
 
@@ -1307,6 +1358,7 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table
         L.prefix = (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp];
         L.ket_start = (band ? b->ws.kst32 : b->ws.kst64) + b->cnt_off[cp];
         L.counter = b->ws.counters + 2 * NCP + 2 * cp + band;
+        L.prim_eps = PRIM_QUARTET_FRAC * o->thresh;
         KernelInfo ki{1, 1};
         ADFT_CUDA(launch_band(band, X, Y, L, 0, 0, s, &ki));
         float best = 1e30f;

@@ -83,6 +83,34 @@ template <> struct Prec<float> {
   static constexpr int BUDGET = 640;
 };
 
+// Primitive-quartet screening inside a kept shell quartet: the primitive
+// pairs of a pair are stored by descending bound Q_p, so the ket primitives q
+// kept for bra primitive p (Q_p Q_q >= eps) are a prefix of the ket's list,
+// and its length n can only shrink from one bra primitive to the next.
+// shrink_kept(qk, qp, eps, n) shortens n for bra primitive bound qp (FP32
+// compares: a bound test needs no more); over all bra primitives of a
+// quartet it reads at most n0 + n1 bounds.  Once n is 0 it stays 0.
+__device__ __forceinline__ int shrink_kept(const float* __restrict__ qk, float qp, float eps, int n) {
+  while (n > 0 && qp * __ldg(qk + n - 1) < eps) --n;
+  return n;
+}
+
+// Warp-sum of the evaluated-work counters of the calling lanes, added once per
+// warp into work[0] (primitive quartets) and work[1] (bra primitives).  All
+// 32 lanes must call it.  (A lane's own counts stay far below 2^32: a launch
+// evaluates at most a few 1e10 primitive quartets over >= 1e4 lanes.)
+__device__ __forceinline__ void flush_work(unsigned long long* work, unsigned pq, unsigned bp) {
+  unsigned long long p = pq, b = bp;
+  for (int o = 16; o > 0; o >>= 1) {
+    p += __shfl_down_sync(0xffffffffu, p, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if (work && (threadIdx.x & 31) == 0 && (p | b)) {
+    atomicAdd(work, p);
+    atomicAdd(work + 1, b);
+  }
+}
+
 // reciprocals 1/(2m+1), m < 32
 __constant__ static const double c_inv_odd64[32] = {
     1.0 / 1, 1.0 / 3, 1.0 / 5, 1.0 / 7, 1.0 / 9, 1.0 / 11, 1.0 / 13, 1.0 / 15, 1.0 / 17, 1.0 / 19, 1.0 / 21,
@@ -260,8 +288,11 @@ __device__ __forceinline__ void prim_R(T alpha, T X, T Y, T Z, const BasisView& 
 // ---------------------------------------------------------------------------
 // Contracted Cartesian block of one shell quartet for the ket components
 // [chunk*CK, chunk*CK + CK): G[ab*CK + k] = (a b | c d)_k.
+// Primitive quartets with Q_p Q_q < eps are skipped; npq and nbp are
+// increased by the primitive quartets and bra primitives evaluated.
 template <typename T, int LA, int LB, int LC, int LD, int CK>
-__device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int ket, int chunk, T* G) {
+__device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int ket, int chunk, T* G, T eps,
+                                              int& npq, int& nbp) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int NAB = NA * NB, NCD = NC * ND;
   constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
@@ -291,7 +322,14 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
 #pragma unroll
   for (int x = 0; x < NAB * CK; ++x) G[x] = T(0);
 
+  const float* __restrict__ qa = bv.pp_q32;
+  const float epsf = (float)eps;
+  int n1e = n1;
   for (int ip = 0; ip < n0; ++ip) {
+    n1e = shrink_kept(qa + off1, __ldg(qa + off0 + ip), epsf, n1e);
+    if (n1e == 0) break;
+    npq += n1e;
+    ++nbp;
     const PrimPair<T> bp = pp[off0 + ip];
     const T o2p = __ldg(Prec<T>::o2p(bv) + off0 + ip);
     T Eab[3][EA];
@@ -303,7 +341,7 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
 #pragma unroll
     for (int x = 0; x < NHAB * CK; ++x) W[x] = T(0);
 
-    for (int iq = 0; iq < n1; ++iq) {
+    for (int iq = 0; iq < n1e; ++iq) {
       const PrimPair<T> kq = pp[off1 + iq];
       const T o2q = __ldg(Prec<T>::o2p(bv) + off1 + iq);
       T Ecd[3][EC];
@@ -544,10 +582,12 @@ struct RtSizes {
 };
 using GenSizes = RtSizes<GEN_E, GEN_NH, GEN_BUDGET>;
 
+// eps > 0 skips the primitive quartets with Q_p Q_q < eps; work (if not NULL)
+// is increased by the primitive quartets and bra primitives evaluated.
 template <typename T, typename S = GenSizes>
 __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView& bv, int bra, int ket, int chunk,
                                               T* G, const T* __restrict__ bra_w = nullptr, int pp_bra = -1,
-                                              int pp_ket = -1) {
+                                              int pp_ket = -1, T eps = T(0), int* work = nullptr) {
   const int LA = C.la, LB = C.lb, LC = C.lc, LD = C.ld, CK = C.ck;
   const int NB = ncart(LB), ND = ncart(LD);
   const int NAB = ncart(LA) * NB, NCD = ncart(LC) * ND;
@@ -574,7 +614,13 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
   for (int x = 0; x < NAB * CK; ++x) G[x] = T(0);
 
 #pragma unroll 1
+  int n1e = n1;
   for (int ip = 0; ip < n0; ++ip) {
+    if (eps > T(0)) {
+      n1e = shrink_kept(bv.pp_q32 + off1, __ldg(bv.pp_q32 + off0 + ip), (float)eps, n1e);
+      if (n1e == 0) break;
+    }
+    if (work) { work[0] += n1e; ++work[1]; }
     const PrimPair<T> bp = pp[off0 + ip];
     const T o2p = __ldg(Prec<T>::o2p(bv) + off0 + ip);
     hermite_E_rt<T>(LA, LB, bp.PAx, bp.PAx + ABx, o2p, Eab);
@@ -582,7 +628,7 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
     hermite_E_rt<T>(LA, LB, bp.PAz, bp.PAz + ABz, o2p, Eab + 2 * EA);
     for (int x = 0; x < nhab * CK; ++x) W[x] = T(0);
 #pragma unroll 1
-    for (int iq = 0; iq < n1; ++iq) {
+    for (int iq = 0; iq < n1e; ++iq) {
       const PrimPair<T> kq = pp[off1 + iq];
       const T o2q = __ldg(Prec<T>::o2p(bv) + off1 + iq);
       hermite_E_rt<T>(LC, LD, kq.PAx, kq.PAx + CDx, o2q, Ecd);
@@ -830,6 +876,7 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
   constexpr int CK = Plan::CK, NCHUNK = Plan::NCHUNK;
   const long long total = (long long)__ldg(a.prefix + a.nbra) * NCHUNK;
   const int lane = threadIdx.x & 31;
+  unsigned cpq = 0, cbp = 0;
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.counter, 32ULL);
@@ -846,10 +893,13 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
       int bra, ket;
       decode_quartet(a, qi, bra, ket);
       T G[NAB * CK];
-      quartet_block<T, LA, LB, LC, LD, CK>(a.bv, bra, ket, chunk, G);
+      int npq = 0, nbp = 0;
+      quartet_block<T, LA, LB, LC, LD, CK>(a.bv, bra, ket, chunk, G, (T)a.prim_eps, npq, nbp);
+      if (chunk == 0) { cpq += npq; cbp += nbp; }  // count each quartet once
       digest<T, LA, LB, LC, LD, CK>(a, bra, ket, chunk, G);
     }
   }
+  flush_work(a.work, cpq, cbp);
 }
 
 template <typename T, int LA, int LB, int LC, int LD>
@@ -862,6 +912,7 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
   const long long total = (long long)__ldg(a.prefix + a.nbra) * C.nchunk;
   const int lane = threadIdx.x & 31;
   T G[NG];
+  unsigned cpq = 0, cbp = 0;
   for (;;) {
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.counter, 32ULL);
@@ -880,10 +931,13 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
       const long long qi = item - (long long)chunk * nq;
       int bra, ket;
       decode_quartet(a, qi, bra, ket);
-      quartet_block_rt<T, S>(C, a.bv, bra, ket, chunk, G);
+      int wk[2] = {0, 0};
+      quartet_block_rt<T, S>(C, a.bv, bra, ket, chunk, G, nullptr, -1, -1, (T)a.prim_eps, wk);
+      if (chunk == 0) { cpq += wk[0]; cbp += wk[1]; }  // count each quartet once
       digest_rt<T>(C, a, bra, ket, chunk, G);
     }
   }
+  flush_work(a.work, cpq, cbp);
 }
 
 #ifdef ADFT_ERI_SCHWARZ

@@ -25,7 +25,7 @@ namespace adft {
 template <typename T>
 __device__ __noinline__ void centre_derivative(const BasisView& bv, int P, int Qk, int la, int lb, int lc, int ld,
                                                int which, const T* __restrict__ D, long n, int oa, int ob, int oc,
-                                               int od, T* out3, T* Gp, T* Gm) {
+                                               int od, T* out3, T* Gp, T* Gm, T eps) {
   const int lup_a = la + (which == 0), lup_b = lb + (which == 1);
   const int ldn_a = la - (which == 0), ldn_b = lb - (which == 1);
   const RtClass Cu = make_rt_class(lup_a, lup_b, lc, ld);
@@ -39,8 +39,8 @@ __device__ __noinline__ void centre_derivative(const BasisView& bv, int P, int Q
   else wts = (const T*)bv.pp_w32 + (which == 0 ? 0 : bv.npp);
   T s0 = 0, s1 = 0, s2 = 0;
   for (int chunk = 0; chunk < Cu.nchunk; ++chunk) {
-    quartet_block_rt<T>(Cu, bv, P, Qk, chunk, Gp, wts);
-    if (has_dn) quartet_block_rt<T>(Cd, bv, P, Qk, chunk, Gm, nullptr);
+    quartet_block_rt<T>(Cu, bv, P, Qk, chunk, Gp, wts, -1, -1, eps);
+    if (has_dn) quartet_block_rt<T>(Cd, bv, P, Qk, chunk, Gm, nullptr, -1, -1, eps);
     const int CK = Cu.ck, kc0 = chunk * CK, nk = min(CK, NCD - kc0);
     for (int ia = 0; ia < NA; ++ia) {
       int ax, ay, az;
@@ -113,9 +113,10 @@ __global__ void __launch_bounds__(JK_THREADS) k_grad_generic(GradLaunch g, int l
       if (sc == sd) w *= T(0.5);
       if (a.same_class && bra == ket) w *= T(0.5);
       T dA[3], dB[3], dC[3];
-      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 0, Dm, nrow, oa, ob, oc, od, dA, Gp, Gm);
-      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 1, Dm, nrow, oa, ob, oc, od, dB, Gp, Gm);
-      centre_derivative<T>(bv, ket, bra, lc, ld, la, lb, 0, Dm, nrow, oc, od, oa, ob, dC, Gp, Gm);
+      const T eps = (T)a.prim_eps;
+      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 0, Dm, nrow, oa, ob, oc, od, dA, Gp, Gm, eps);
+      centre_derivative<T>(bv, bra, ket, la, lb, lc, ld, 1, Dm, nrow, oa, ob, oc, od, dB, Gp, Gm, eps);
+      centre_derivative<T>(bv, ket, bra, lc, ld, la, lb, 0, Dm, nrow, oc, od, oa, ob, dC, Gp, Gm, eps);
       const int ta = bv.shell_atom[sa], tb = bv.shell_atom[sb], tc = bv.shell_atom[sc], td = bv.shell_atom[sd];
       for (int k = 0; k < 3; ++k) {
         atomicAdd(g.grad + 3 * ta + k, (double)(w * dA[k]));

@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_grad_coop(GradLaunch gl
   const BasisView& bv = a.bv;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
   const T* __restrict__ o2pa = Prec<T>::o2p(bv);
+  const float* __restrict__ qa = bv.pp_q32;
+  const float eps = (float)a.prim_eps;
   const T* __restrict__ wts = nullptr;  // 2a of every primitive pair, then 2b
   if constexpr (sizeof(T) == 8) wts = (const T*)bv.pp_w64; else wts = (const T*)bv.pp_w32;
   int cur_ta = -1, cur_tb = -1;
@@ -139,7 +141,10 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_grad_coop(GradLaunch gl
             CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
     T sA[3] = {T(0), T(0), T(0)}, sB[3] = {T(0), T(0), T(0)};
 
+    int n1e = n1;
     for (int ip = 0; ip < n0; ++ip) {
+      n1e = shrink_kept(qa + off1, __ldg(qa + off0 + ip), eps, n1e);  // same in every lane
+      if (n1e == 0) break;
       const PrimPair<T> bp = pp[off0 + ip];
       const T o2p = __ldg(o2pa + off0 + ip);
       const T ta2 = __ldg(wts + off0 + ip), tb2 = __ldg(wts + bv.npp + off0 + ip);
@@ -151,8 +156,8 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_grad_coop(GradLaunch gl
 #pragma unroll
       for (int x = 0; x < NHAB1 * CK; ++x) W[x] = T(0);
       __syncwarp(gmask);
-      for (int q0 = 0; q0 < n1; q0 += P::SLOTS) {
-        const int nv = min(P::SLOTS, n1 - q0);
+      for (int q0 = 0; q0 < n1e; q0 += P::SLOTS) {
+        const int nv = min(P::SLOTS, n1e - q0);
         if (gl < nv) {
           const int iq = off1 + q0 + gl;
           const PrimPair<T> kq = pp[iq];

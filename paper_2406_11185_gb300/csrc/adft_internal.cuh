@@ -59,6 +59,7 @@ struct BasisView {
   const float* pp_o2p32;
   const double* pp_w64;    // [2][npp]: 2 a and 2 b of every primitive pair
   const float* pp_w32;
+  const float* pp_q32;     // [npp] primitive-pair bound Q_p; descending within each pair
   long long npp;
   // several molecules (a batch): molecule of each pair, offset and row length
   // of the molecule's block in the packed Cartesian matrices; NULL = one
@@ -95,6 +96,8 @@ struct JKLaunch {
   double* K;
   const int* abort_flag;    // device flag polled between work chunks
   int* status;              // device status word
+  double prim_eps;          // primitive quartets with Q_p Q_q below this are skipped
+  unsigned long long* work; // [2]: primitive quartets and bra primitives evaluated, or NULL
 };
 
 struct GradLaunch {
@@ -129,6 +132,9 @@ cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, co
 // Primitive pairs whose bound Qp * max(Qp) is at or below this are dropped at
 // basis creation (1e-3 of the paper's default tolerance 1e-12).
 constexpr double PRIM_EPS = 1e-15;
+// Inside a kept shell quartet, primitive quartets with Q_p Q_q below
+// PRIM_QUARTET_FRAC * thresh are skipped (each is bounded by that value).
+constexpr double PRIM_QUARTET_FRAC = 1e-4;
 // Boys tables in device memory of the current device (built once).
 cudaError_t boys_tables(const double** t64, const float** t32);
 

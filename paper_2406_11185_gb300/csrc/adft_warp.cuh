@@ -90,6 +90,9 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_warp(JKLaunch a) {
   const BasisView& bv = a.bv;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
   const T* __restrict__ o2pa = Prec<T>::o2p(bv);
+  const float* __restrict__ qa = bv.pp_q32;
+  const float eps = (float)a.prim_eps;
+  unsigned cpq = 0, cbp = 0;  // evaluated work (lane 0)
 
   // this lane's bra Hermite indices: offsets of R(t+tau, u+nu, v+phi) as
   // T3(n + sigma) + T2(m + mu) + v + phi, sigma = tau+nu+phi, mu = nu+phi
@@ -134,7 +137,11 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_warp(JKLaunch a) {
                      from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2))};
     for (int x = lane; x < NAB * NCD; x += 32) Gsm[x] = T(0);
 
+    int n1e = n1;
     for (int ip = 0; ip < n0; ++ip) {
+      n1e = shrink_kept(qa + off1, __ldg(qa + off0 + ip), eps, n1e);  // same in every lane
+      if (n1e == 0) break;
+      if (lane == 0) { cpq += n1e; ++cbp; }
       const PrimPair<T> bp = pp[off0 + ip];
       const T o2p = __ldg(o2pa + off0 + ip);
       if (lane < 3) {
@@ -158,8 +165,8 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_warp(JKLaunch a) {
                    Eab[2 * EA + (az * (LB + 1) + bz) * NTA + v];
       }
       __syncwarp();
-      for (int q0 = 0; q0 < n1; q0 += SL) {
-        const int nv = min(SL, n1 - q0);
+      for (int q0 = 0; q0 < n1e; q0 += SL) {
+        const int nv = min(SL, n1e - q0);
         if (lane < nv) {
           const int iq = off1 + q0 + lane;
           const PrimPair<T> kq = pp[iq];
@@ -255,4 +262,5 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_warp(JKLaunch a) {
     digest_coop<T, LA, LB, LC, LD>(a, bra, ket, lane, 32, Gsm);
     __syncwarp();
   }
+  flush_work(a.work, cpq, cbp);
 }

@@ -112,6 +112,25 @@ def test_alternative_kernel_variant_parity(precision):
         assert abs(E - Er) <= TOL_E_MIXED and dj <= 1e-5 and dk <= 1e-5
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_primitive_screening_counts(precision):
+    """A build reports the primitive quartets its kernels evaluated (after
+    primitive-quartet screening); the plan reports the unscreened count."""
+    mol, opt, D = _case("small")
+    b = adft.Basis.from_molecule(mol)
+    Dt = torch.from_numpy(D).cuda()
+    adft.adft_jk_build(b, Dt, thresh=opt["thresh"], precision=precision)
+    st = adft.adft_jk_last_stats(b)
+    plan, _ = adft.adft_jk_plan(b, Dt, thresh=opt["thresh"], precision=precision)
+    print(f"{precision}: evaluated {st} planned {plan}")
+    for k in ("quartets_fp64", "quartets_fp32", "quartets_total"):
+        assert st[k] == plan[k]
+    for band in ("fp64", "fp32"):
+        assert st[f"prim_quartets_{band}"] <= plan[f"prim_quartets_{band}"]
+        assert st[f"flops_{band}"] <= plan[f"flops_{band}"] * (1 + 1e-9)
+    assert st["prim_quartets_fp64"] > 0
+
+
 def test_schwarz_bounds_match_oracle():
     mol, opt, D = _case("tiny_f")
     b = adft.Basis.from_molecule(mol)
