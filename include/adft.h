@@ -238,6 +238,12 @@ int adft_batch_last_timings(adft_batch* bt, double* ms);
 /* The autotuner of the batch's class-pair kernels (see adft_autotune). */
 int adft_batch_autotune(adft_batch* bt, const double* D_packed, const adft_opts* opts, int* table, double* ms);
 
+/* Install a launch-shape table (adft_autotune's layout and encoding) in the
+ * batch, e.g. one tuned on a smaller batch of the same kind of molecules.
+ * The batch's captured CUDA graph is dropped and re-captured on the next
+ * call.  ADFT_ERR_ARG as for adft_set_tuning. */
+int adft_batch_set_tuning(adft_batch* bt, const int* table);
+
 void adft_batch_destroy(adft_batch* bt);
 
 /* ---- energy without allocation ------------------------------------------ */

@@ -35,6 +35,7 @@ EXPORTED = [
     "adft_basis_destroy", "adft_batch_create", "adft_batch_offsets", "adft_batch_grad_offsets", "adft_batch_jk",
     "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version", "adft_autotune",
     "adft_set_tuning", "adft_jk_plan", "adft_energy_static", "adft_batch_last_stats", "adft_batch_last_timings", "adft_batch_autotune",
+    "adft_batch_set_tuning",
 ]
 
 
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH):
     L.adft_batch_last_stats.argtypes = [vp, ctypes.POINTER(adft_stats)]
     L.adft_batch_last_timings.argtypes = [vp, dp]
     L.adft_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(adft_opts), ctypes.POINTER(ctypes.c_int), dp]
+    L.adft_batch_set_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.adft_energy_static.argtypes = [vp, vp, vp, ip, vp, vp]
     L.adft_status_string.argtypes = [ip]
     L.adft_status_string.restype = ctypes.c_char_p
@@ -372,6 +374,15 @@ def adft_batch_autotune(batch: Batch, D_packed, thresh=1e-10, split=1e-5, precis
     _check(load().adft_batch_autotune(batch.handle, ctypes.c_void_p(D_packed.data_ptr()), ctypes.byref(o), tab,
                                       None), "adft_batch_autotune")
     return np.array(tab[:], dtype=np.int32).reshape(2, NCP)
+
+
+def adft_batch_set_tuning(batch: Batch, table) -> None:
+    """Install a [2, 55] launch-shape table in a batch (adft_autotune's encoding)."""
+    t = np.ascontiguousarray(np.asarray(table, dtype=np.int32).reshape(-1))
+    if t.size != 2 * NCP:
+        raise ValueError("table must hold 2 x 55 entries")
+    _check(load().adft_batch_set_tuning(batch.handle, t.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+           "adft_batch_set_tuning")
 
 
 def adft_energy_static(D, J, K, stream=None):

@@ -179,24 +179,37 @@ __device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket,
   }
 }
 
-// Group size: the number of lanes sharing one quartet.  It maximises the
-// useful fraction of the warp, (lanes in whole groups / 32) * (NCD / (GS * CK)),
-// with CK = ceil(NCD / GS) ket components per lane, under the register budget
-// NHAB * CK <= wmax for the per-lane W block and the shared-memory budget of
-// at least 4 warps per block (one per SM sub-partition).
-__host__ __device__ constexpr int coop_slots(int gs) { return gs < COOP_SLOT_CAP ? gs : COOP_SLOT_CAP; }
-__host__ __device__ constexpr int coop_group_size(int ncd, int nhab, int wmax, int nh, int ec, int nab, int ea,
-                                                  int tsize) {
-  int best = 32 < ncd ? 32 : ncd;
+// Group shape: GS lanes share one quartet and stage SLOTS ket primitives at a
+// time (SLOTS <= GS, one primitive per lane).  The shape maximises the useful
+// fraction of the warp, (lanes in whole groups / 32) * (NCD / (GS * CK)) with
+// CK = ceil(NCD / GS) ket components per lane, under the register budget
+// NHAB * CK <= wmax for the per-lane W block and the shared-memory budget of at
+// least 4 warps per block (one per SM sub-partition); for each GS the largest
+// SLOTS in {min(GS, 8), 4, 2, 1} that fits is taken, and between equally
+// useful shapes the one with more slots wins.
+struct CoopShape {
+  int gs, slots;
+};
+__host__ __device__ constexpr CoopShape coop_shape(int ncd, int nhab, int wmax, int nh, int ec, int nab, int ea,
+                                                   int tsize) {
+  CoopShape best{32 < ncd ? 32 : ncd, 1};
   double best_u = -1.0;
   for (int gs = 1; gs <= 32 && gs <= ncd; ++gs) {
     const int ck = (ncd + gs - 1) / gs;
     if (nhab * ck > wmax) continue;
-    const int group = coop_slots(gs) * (nh + 3 * ec) + nab * ncd + 3 * ea;
-    const int warp_bytes = (32 / gs) * group * tsize;
-    if (COOP_SMEM_BUDGET / warp_bytes < 4) continue;
+    int slots = gs < COOP_SLOT_CAP ? gs : COOP_SLOT_CAP;
+    bool ok = false;
+    for (; slots >= 1; slots = (slots > 4 ? 4 : slots / 2)) {
+      const int group = slots * (nh + 3 * ec) + nab * ncd + 3 * ea;
+      const int warp_bytes = (32 / gs) * group * tsize;
+      if (COOP_SMEM_BUDGET / warp_bytes >= 4) { ok = true; break; }
+    }
+    if (!ok) continue;
     const double u = (double)((32 / gs) * gs) / 32.0 * (double)ncd / (double)(gs * ck);
-    if (u > best_u + 1e-9) { best_u = u; best = gs; }
+    if (u > best_u + 1e-9 || (u > best_u - 1e-9 && slots > best.slots)) {
+      best_u = u;
+      best = CoopShape{gs, slots};
+    }
   }
   return best;
 }
@@ -209,10 +222,11 @@ struct CoopPlan {
   static constexpr int NHAB = nherm(LAB), NH = nherm(L);
   static constexpr int EA = (LA + 1) * (LB + 1) * (LAB + 1), EC = (LC + 1) * (LD + 1) * (LCD + 1);
   static constexpr int WMAX = (sizeof(T) == 8 ? 80 : 100);
-  static constexpr int GS = coop_group_size(NCD, NHAB, WMAX, NH, EC, NAB, EA, (int)sizeof(T));
+  static constexpr CoopShape SHAPE = coop_shape(NCD, NHAB, WMAX, NH, EC, NAB, EA, (int)sizeof(T));
+  static constexpr int GS = SHAPE.gs;
   static constexpr int CK = (NCD + GS - 1) / GS;
   static constexpr int NGW = 32 / GS;
-  static constexpr int SLOTS = coop_slots(GS);
+  static constexpr int SLOTS = SHAPE.slots;
   static constexpr int SLOT = NH + 3 * EC;
   static constexpr int GROUP = SLOTS * SLOT + NAB * NCD + 3 * EA;
   static constexpr int WARP_BYTES = NGW * GROUP * (int)sizeof(T);

@@ -1012,10 +1012,28 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
     BasisView v = view(b);
     v.pair_mol = nullptr;  // bounds need no packed offsets
     ADFT_CUDA(cudaMemset(b->d_pair_Q, 0, (size_t)b->npair * sizeof(double)));
+    // scratch of the partial diagonals: the largest class's n * NAB * maxp
+    std::vector<int> maxp(NCLS, 0);
+    size_t part_n = 0;
+    for (int X = 0; X < NCLS; ++X) {
+      for (int i = b->cls_first[X]; i < b->cls_first[X + 1]; ++i) maxp[X] = std::max(maxp[X], ppn[i]);
+      const size_t nab = (size_t)ncart(cls_la(X)) * ncart(cls_lb(X));
+      part_n = std::max(part_n, (size_t)(b->cls_first[X + 1] - b->cls_first[X]) * nab * (size_t)maxp[X]);
+    }
+    // (freed once the bounds are read back: it is the largest temporary here)
+    double* d_part = nullptr;
+    if (cudaMalloc((void**)&d_part, std::max<size_t>(part_n, 1) * sizeof(double)) != cudaSuccess) {
+      set_error("cudaMalloc of the Schwarz scratch failed");
+      return ADFT_ERR_OOM;
+    }
+    struct PartFree {
+      double* p;
+      ~PartFree() { cudaFree(p); }
+    } part_guard{d_part};
     for (int X = 0; X < NCLS; ++X) {
       const int n = b->cls_first[X + 1] - b->cls_first[X];
       if (n == 0) continue;
-      cudaError_t e = launch_schwarz(X, v, b->cls_first[X], n, b->d_pair_Q, 0);
+      cudaError_t e = launch_schwarz(X, v, b->cls_first[X], n, maxp[X], d_part, b->d_pair_Q, 0);
       if (e != cudaSuccess) { set_error(std::string("schwarz: ") + cudaGetErrorString(e)); return ADFT_ERR_CUDA; }
       const int last = b->cls_first[X + 1] - 1;
       const int npp_cls = ppoff[last] + ppn[last] - ppoff[b->cls_first[X]];
@@ -1543,6 +1561,17 @@ int adft_batch_autotune(adft_batch* bt, const double* D, const adft_opts* o, int
     bt->exec = nullptr; bt->graph = nullptr; bt->has_graph = false;
   }
   return adft_autotune(bt->b, D, o, table, ms);
+}
+
+int adft_batch_set_tuning(adft_batch* bt, const int* table) {
+  if (!bt) { set_error("NULL batch"); return ADFT_ERR_ARG; }
+  const int st = adft_set_tuning(bt->b, table);
+  if (st) return st;
+  if (bt->has_graph) {  // the captured graph holds the old launch shapes
+    cudaGraphExecDestroy(bt->exec); cudaGraphDestroy(bt->graph);
+    bt->exec = nullptr; bt->graph = nullptr; bt->has_graph = false;
+  }
+  return ADFT_OK;
 }
 
 void adft_batch_destroy(adft_batch* bt) {

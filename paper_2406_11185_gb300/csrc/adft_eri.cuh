@@ -941,25 +941,43 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
 }
 
 #ifdef ADFT_ERI_SCHWARZ
-// Schwarz bounds of the pairs of one class, first step: max |(mn|mn)| over
-// the components of one chunk of one pair (one thread per (pair, chunk)),
-// combined with an integer atomicMax on the bits of the non-negative double
-// (its ordering matches); Qmax must be zero on entry and the caller takes
-// the square root.
-static __global__ void __launch_bounds__(JK_THREADS) k_schwarz_generic(BasisView bv, RtClass C, int first, int n,
-                                                                 unsigned long long* Qmax) {
+// Schwarz bounds of the pairs of one class, first step: one thread per
+// (pair i, chunk of components, bra primitive pair p) evaluates the diagonal
+// elements (mn|mn) of its chunk with the bra restricted to p and every ket
+// primitive, into part[(i * NAB + mn) * maxp + p].  Splitting over p keeps
+// each thread's serial work to one row of primitive quartets.
+static __global__ void __launch_bounds__(JK_THREADS) k_schwarz_part(BasisView bv, RtClass C, int first, int n,
+                                                                    int maxp, double* part) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)n * C.nchunk) return;
-  const int pr = first + (int)(t / C.nchunk), chunk = (int)(t % C.nchunk);
+  const long long per = (long long)C.nchunk * maxp;
+  if (t >= (long long)n * per) return;
+  const int i = (int)(t / per), r = (int)(t % per);
+  const int chunk = r / maxp, ip = r % maxp;
+  const int pr = first + i;
+  if (ip >= bv.pair_pp_n[pr]) return;
   const int NAB = ncart(C.la) * ncart(C.lb);
-  double mx = 0.0;
   double G[GEN_BUDGET];
-  quartet_block_rt<double>(C, bv, pr, pr, chunk, G);
+  quartet_block_rt<double>(C, bv, pr, pr, chunk, G, nullptr, bv.pair_pp_off[pr] + ip, -1);
   for (int k = 0; k < C.ck; ++k) {
     const int kc = chunk * C.ck + k;
-    if (kc < NAB) mx = fmax(mx, fabs(G[kc * C.ck + k]));
+    if (kc < NAB) part[((long long)i * NAB + kc) * maxp + ip] = G[kc * C.ck + k];
   }
-  atomicMax(Qmax + pr, (unsigned long long)__double_as_longlong(mx));
+}
+
+// Second step: (mn|mn) = sum over p in order (the same every run), and
+// Qmax[pr] = max over mn of |(mn|mn)| by an integer atomicMax on the bits of
+// the non-negative double (its ordering matches; the maximum does not depend
+// on the order).  Qmax must be zero on entry; the caller takes the root.
+static __global__ void k_schwarz_reduce(BasisView bv, int first, int n, int nab, int maxp, const double* part,
+                                        unsigned long long* Qmax) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * nab) return;
+  const int i = (int)(t / nab);
+  const int np = bv.pair_pp_n[first + i];
+  const double* src = part + t * maxp;
+  double s = 0.0;
+  for (int p = 0; p < np; ++p) s += src[p];
+  atomicMax(Qmax + first + i, (unsigned long long)__double_as_longlong(fabs(s)));
 }
 
 // Primitive-pair bounds of the pairs of one class: Qp = sqrt(max |[mn|mn]_p|)

@@ -17,13 +17,18 @@ template cudaError_t launch_one<double, 9, 7>(const JKLaunch&, int, int, cudaStr
 template cudaError_t launch_one<double, 9, 8>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 template cudaError_t launch_one<double, 9, 9>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 
-cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Qmax, cudaStream_t s) {
+cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, int maxp, double* part, double* Qmax,
+                           cudaStream_t s) {
   if (X < 0 || X >= NCLS) return cudaErrorInvalidValue;
+  if (n <= 0 || maxp <= 0) return cudaSuccess;
   const RtClass C = make_rt_class(cls_la(X), cls_lb(X), cls_la(X), cls_lb(X));
-  const long long threads = (long long)n * C.nchunk;
-  const int blocks = (int)((threads + JK_THREADS - 1) / JK_THREADS);
-  if (blocks > 0)
-    k_schwarz_generic<<<blocks, JK_THREADS, 0, s>>>(bv, C, first, n, reinterpret_cast<unsigned long long*>(Qmax));
+  const int nab = ncart(cls_la(X)) * ncart(cls_lb(X));
+  const long long t1 = (long long)n * C.nchunk * maxp, t2 = (long long)n * nab;
+  k_schwarz_part<<<(unsigned)((t1 + JK_THREADS - 1) / JK_THREADS), JK_THREADS, 0, s>>>(bv, C, first, n, maxp, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_schwarz_reduce<<<(unsigned)((t2 + 255) / 256), 256, 0, s>>>(bv, first, n, nab, maxp, part,
+                                                                reinterpret_cast<unsigned long long*>(Qmax));
   return cudaGetLastError();
 }
 

@@ -38,10 +38,11 @@ struct GradPlan {
   static constexpr int EA1 = (LA + 2) * (LB + 2) * NT1;         // bra E with l_a + 1, l_b + 1
   static constexpr int EC = (LC + 1) * (LD + 1) * (LCD + 1);
   static constexpr int WMAX = (sizeof(T) == 8 ? 112 : 128);
-  static constexpr int GS = coop_group_size(NCD, NHAB1, WMAX, NH1, EC, NAB, EA1, (int)sizeof(T));
+  static constexpr CoopShape SHAPE = coop_shape(NCD, NHAB1, WMAX, NH1, EC, NAB, EA1, (int)sizeof(T));
+  static constexpr int GS = SHAPE.gs;
   static constexpr int CK = (NCD + GS - 1) / GS;
   static constexpr int NGW = 32 / GS;
-  static constexpr int SLOTS = coop_slots(GS);
+  static constexpr int SLOTS = SHAPE.slots;
   static constexpr int SLOT = NH1 + 3 * EC;
   static constexpr int RED = 6 * GS;                             // group reduction scratch
   // slot region: R and ket E tables of the ket primitives, then W of a bra

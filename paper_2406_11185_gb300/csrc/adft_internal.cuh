@@ -125,8 +125,10 @@ cudaError_t launch_jk_fp32(int X, int Y, const JKLaunch& a, int grid, int varian
 cudaError_t launch_grad_fp64(int X, int Y, const GradLaunch& a, int sms, cudaStream_t s);
 cudaError_t launch_grad_fp32(int X, int Y, const GradLaunch& a, int sms, cudaStream_t s);
 // Qmax[pr] = max |(mn|mn)| of the pairs [first, first + n) of class X (zeroed
-// by the caller; Q = sqrt(Qmax)).
-cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, double* Qmax, cudaStream_t s);
+// by the caller; Q = sqrt(Qmax)).  maxp: the largest primitive-pair count of
+// those pairs; part: scratch of n * ncart(la) ncart(lb) * maxp doubles.
+cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, int maxp, double* part, double* Qmax,
+                           cudaStream_t s);
 cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, const int* pp_pair, int npp_class,
                                 double* Qp, cudaStream_t s);
 // Primitive pairs whose bound Qp * max(Qp) is at or below this are dropped at

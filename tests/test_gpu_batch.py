@@ -78,3 +78,26 @@ def test_autotune_keeps_results():
     J1, K1 = adft.adft_jk_build(b, D, thresh=opt["thresh"], precision="mixed")
     assert torch.max(torch.abs(J1 - J0)).item() <= 1e-12 * torch.max(torch.abs(J0)).item()
     assert torch.max(torch.abs(K1 - K0)).item() <= 1e-12 * torch.max(torch.abs(K0)).item()
+
+
+def test_batch_tuning_from_sub_batch():
+    """A table tuned on a sub-batch, installed with adft_batch_set_tuning,
+    drops the captured graph and leaves the results unchanged."""
+    mols, Ds = _small_batch()
+    thresh, split = 1e-10, 1e-5
+    bases = [adft.Basis.from_molecule(m) for m in mols]
+    bt = adft.Batch(bases)
+    Dt = [torch.from_numpy(D).cuda() for D in Ds]
+    Dp = bt.pack(Dt)
+    r0 = tuple(x.clone() for x in adft.adft_batch_jk(bt, Dp, thresh=thresh, split=split, precision="mixed",
+                                                      grad=True))
+    sub = adft.Batch(bases[:2])
+    tab = adft.adft_batch_autotune(sub, sub.pack(Dt[:2]), thresh=thresh, split=split, precision="mixed")
+    adft.adft_batch_set_tuning(bt, tab)
+    bad = tab.copy()
+    bad[0, 0] = 0  # zero blocks per SM
+    with pytest.raises(adft.AdftError):
+        adft.adft_batch_set_tuning(bt, bad)
+    r1 = adft.adft_batch_jk(bt, Dp, thresh=thresh, split=split, precision="mixed", grad=True)
+    for a, b in zip(r0, r1):
+        assert torch.max(torch.abs(a - b)).item() <= 1e-11 * max(1.0, torch.max(torch.abs(a)).item())
