@@ -47,3 +47,49 @@ def test_null_arguments_rejected_without_gpu(lib):
     n = ctypes.c_int()
     assert lib.adft_basis_nbf(None, ctypes.byref(n)) == adft.ADFT_ERR_ARG
     assert len(adft.last_error()) > 0
+
+
+def _shell_args(shells):
+    """ctypes adft_shell array for [(atom, l, exps, coefs)] (arrays kept alive in the result)."""
+    keep = []
+    arr = (adft.adft_shell * len(shells))()
+    for i, (atom, l, exps, coefs) in enumerate(shells):
+        e = (ctypes.c_double * len(exps))(*exps)
+        c = (ctypes.c_double * len(coefs))(*coefs)
+        keep += [e, c]
+        arr[i].atom, arr[i].l, arr[i].nprim = atom, l, len(exps)
+        arr[i].exps = ctypes.cast(e, ctypes.POINTER(ctypes.c_double))
+        arr[i].coefs = ctypes.cast(c, ctypes.POINTER(ctypes.c_double))
+    return arr, keep
+
+
+@pytest.mark.parametrize("bad", ["l_too_high", "too_many_prims", "zero_prims", "bad_exponent", "bad_atom",
+                                 "nan_coordinate", "bad_spherical"])
+def test_invalid_basis_rejected_before_any_device_work(lib, bad):
+    """Every argument error of adft_basis_create is caught on the host, before
+    the first CUDA call, so these run without a GPU."""
+    xyz = [0.0, 0.0, 0.0, 0.0, 0.0, 1.4]
+    shells = [(0, 0, [3.0, 0.5], [0.4, 0.7]), (1, 1, [1.1], [1.0])]
+    spherical = 1
+    if bad == "l_too_high":
+        shells[1] = (1, adft.ADFT_LMAX + 1, [1.1], [1.0])
+    elif bad == "too_many_prims":
+        n = adft.ADFT_MAX_NPRIM + 1
+        shells[0] = (0, 0, [0.1 * 1.5 ** k for k in range(n)], [1.0] * n)
+    elif bad == "zero_prims":
+        shells[0] = (0, 0, [], [])
+    elif bad == "bad_exponent":
+        shells[0] = (0, 0, [3.0, -0.5], [0.4, 0.7])
+    elif bad == "bad_atom":
+        shells[1] = (2, 1, [1.1], [1.0])
+    elif bad == "nan_coordinate":
+        xyz[4] = float("nan")
+    elif bad == "bad_spherical":
+        spherical = 2
+    arr, keep = _shell_args(shells)
+    cxyz = (ctypes.c_double * len(xyz))(*xyz)
+    out = ctypes.c_void_p()
+    st = lib.adft_basis_create(cxyz, 2, arr, len(shells), spherical, ctypes.byref(out))
+    assert st == adft.ADFT_ERR_ARG, (bad, st, adft.last_error())
+    assert not out.value
+    assert len(adft.last_error()) > 0
