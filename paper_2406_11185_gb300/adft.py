@@ -232,6 +232,62 @@ def adft_jk_grad(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", ch
     return g
 
 
+_JK_ENERGY_FN = None
+
+
+def _jk_energy_function():
+    """The torch.autograd.Function of jk_energy (created on first use, so that
+    importing this module does not import torch)."""
+    global _JK_ENERGY_FN
+    if _JK_ENERGY_FN is not None:
+        return _JK_ENERGY_FN
+    import torch
+
+    class JKEnergy(torch.autograd.Function):
+        """E_JK(D, R) = 1/2 tr(DJ) - 1/4 tr(DK) as a function of the nuclear
+        coordinates R.  Forward: adft_jk_energy on a basis built at R.
+        Backward: grad_output times adft_jk_grad, the derivative integrals
+        contracted with D (x) D on the GPU, recomputed rather than stored.
+        D receives no gradient."""
+
+        @staticmethod
+        def forward(ctx, D, coords, shells, spherical, thresh, split, precision):
+            xyz = coords.detach().to("cpu", torch.float64).numpy()
+            basis = Basis(xyz, shells, spherical)
+            E = adft_jk_energy(basis, D, thresh=thresh, split=split, precision=precision, check=False,
+                               on_device=True)
+            ctx.basis = basis
+            ctx.opts = (thresh, split, precision)
+            ctx.coords_meta = (coords.device, coords.dtype)
+            ctx.save_for_backward(D)
+            return E.reshape(())
+
+        @staticmethod
+        def backward(ctx, grad_E):
+            (D,) = ctx.saved_tensors
+            thresh, split, precision = ctx.opts
+            g = adft_jk_grad(ctx.basis, D, thresh=thresh, split=split, precision=precision, check=False)
+            device, dtype = ctx.coords_meta
+            return None, (grad_E.to(g.device) * g).to(device, dtype), None, None, None, None, None
+
+    _JK_ENERGY_FN = JKEnergy
+    return JKEnergy
+
+
+def jk_energy(D, coords, shells, spherical=True, thresh=1e-12, split=1e-5, precision="fp64"):
+    """Differentiable E_JK (torch scalar on D's device) of density D (CUDA,
+    float64, nbf x nbf) at nuclear coordinates coords (natom x 3, bohr; any
+    device), basis shells [(atom, l, exps, coefs)].  E.backward() fills
+    coords.grad with dE/dR from the GPU gradient kernels."""
+    return _jk_energy_function().apply(D, coords, shells, spherical, thresh, split, precision)
+
+
+def __getattr__(name):
+    if name == "JKEnergy":
+        return _jk_energy_function()
+    raise AttributeError(name)
+
+
 def adft_jk_last_stats(basis: Basis) -> dict:
     st = adft_stats()
     _check(load().adft_jk_last_stats(basis.handle, ctypes.byref(st)), "adft_jk_last_stats")

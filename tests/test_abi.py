@@ -93,3 +93,9 @@ def test_invalid_basis_rejected_before_any_device_work(lib, bad):
     assert st == adft.ADFT_ERR_ARG, (bad, st, adft.last_error())
     assert not out.value
     assert len(adft.last_error()) > 0
+
+
+def test_autograd_function_available_without_gpu():
+    torch = pytest.importorskip("torch")
+    assert issubclass(adft.JKEnergy, torch.autograd.Function)
+    assert adft._jk_energy_function() is adft.JKEnergy

@@ -71,3 +71,23 @@ def test_grad_mixed_error_reported():
     err_o = np.max(np.abs(gmx - _oracle_grad("small", mol, D, opt["thresh"])))
     print(f"mixed gradient: max|grad_mixed - grad_fp64| = {err:.2e}, vs oracle {err_o:.2e}")
     assert err <= 1e-5 and err_o <= 1e-5
+
+
+def test_autograd_energy_backward_matches_gradient_kernel_and_oracle():
+    mol, opt, D = _case("tiny")
+    Dt = torch.from_numpy(D).cuda()
+    coords = torch.tensor(mol.atoms, dtype=torch.float64, requires_grad=True)
+    E = adft.jk_energy(Dt, coords, mol.shells, mol.spherical, thresh=opt["thresh"])
+    E.backward()
+    b = adft.Basis.from_molecule(mol)
+    g_kernel = adft.adft_jk_grad(b, Dt, thresh=opt["thresh"]).cpu().numpy()
+    g_oracle = _oracle_grad("tiny", mol, D, opt["thresh"])
+    assert coords.grad is not None and coords.grad.shape == (mol.natom, 3)
+    assert abs(E.item() - adft.adft_jk_energy(b, Dt, thresh=opt["thresh"])) <= 1e-12 * abs(E.item())
+    # same kernels; only the order of the FP64 atomic additions may differ
+    assert np.max(np.abs(coords.grad.numpy() - g_kernel)) <= 1e-12 * np.max(np.abs(g_kernel))
+    assert np.max(np.abs(coords.grad.numpy() - g_oracle)) <= 1e-9
+    # chain rule through a scaled loss
+    coords.grad = None
+    (3.0 * adft.jk_energy(Dt, coords, mol.shells, mol.spherical, thresh=opt["thresh"])).backward()
+    assert np.max(np.abs(coords.grad.numpy() - 3.0 * g_kernel)) <= 3e-12 * np.max(np.abs(g_kernel))
