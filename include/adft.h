@@ -100,13 +100,17 @@ typedef struct {
   void* stream;    /* cudaStream_t, NULL = legacy default stream */
 } adft_opts;
 
-/* Per-call statistics of the last J/K build (host copies). */
+/* Per-call statistics of the last J/K build (host copies).  After a build
+ * the primitive counts and flops are what the kernels evaluated: inside a
+ * kept shell quartet, primitive quartets with Q_p Q_q < 1e-4 * thresh are
+ * skipped.  After adft_jk_plan (no kernels run) they are the counts before
+ * that primitive screening. */
 typedef struct {
   int64_t quartets_fp64;     /* shell quartets evaluated in FP64 */
   int64_t quartets_fp32;     /* shell quartets evaluated in FP32 */
   int64_t quartets_total;    /* unique shell quartets before screening */
-  int64_t prim_quartets_fp64; /* primitive quartets inside the FP64 ones */
-  int64_t prim_quartets_fp32; /* primitive quartets inside the FP32 ones */
+  int64_t prim_quartets_fp64; /* primitive quartets evaluated inside the FP64 ones */
+  int64_t prim_quartets_fp32; /* primitive quartets evaluated inside the FP32 ones */
   double flops_fp64;         /* counted FP64 flops of the ERI + digestion kernels */
   double flops_fp32;         /* counted FP32 flops of the ERI + digestion kernels */
 } adft_stats;
@@ -117,7 +121,9 @@ typedef struct {
  * different shells": every shell is one segmented contraction), evaluates the
  * Schwarz bounds Q_ab on the GPU and sorts the pairs of each
  * angular-momentum class (l_a >= l_b) by descending Q (the angular-momentum
- * reordering of Sec. 1.2.2).  Synchronous.
+ * reordering of Sec. 1.2.2).  Primitive pairs whose bound Q_p times the
+ * largest Q_p is at most 1e-15 are dropped; the others are kept in order of
+ * descending Q_p.  Synchronous.
  *   atom_xyz: host [natom*3] bohr.  shells: host [nshell].
  *   spherical: 1 = spherical functions, 0 = Cartesian functions.
  *   out: receives the handle; release it with adft_basis_destroy. */
