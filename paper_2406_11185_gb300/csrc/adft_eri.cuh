@@ -1015,9 +1015,22 @@ template <typename T, int X, int Y>
 cudaError_t launch_one(const JKLaunch& a, int grid, int variant, cudaStream_t s, KernelInfo* info);
 
 #ifndef ADFT_ERI_DECLARE_ONLY
+// A flag per CUDA device: a kernel's dynamic shared-memory attribute is set
+// once per device (it does not carry over to another device).  Concurrent
+// first calls may both set it, which is harmless.
+struct PerDeviceFlag {
+  static constexpr int MAXDEV = 64;
+  bool set[MAXDEV] = {};
+  bool& current() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= MAXDEV) d = 0;
+    return set[d];
+  }
+};
+
 // Launch kern with smem bytes of dynamic shared memory, or, with info, report
 // how many blocks of it fit on one SM.  configured: the instantiation's
-// one-time flag for the shared-memory attribute.
+// one-time flag (for the current device) for the shared-memory attribute.
 template <typename Kern>
 static cudaError_t start(Kern kern, const JKLaunch& a, int grid, int threads, int smem, bool& configured,
                          int variants, cudaStream_t s, KernelInfo* info) {
@@ -1040,8 +1053,8 @@ cudaError_t launch_one(const JKLaunch& a, int grid, int variant, cudaStream_t s,
   if constexpr (X < Y) {
     return cudaErrorInvalidValue;
   } else if constexpr (is_small_class(LA, LB, LC, LD)) {
-    static bool configured = false;
-    return start(k_jk<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured, 1, s, info);
+    static PerDeviceFlag configured;
+    return start(k_jk<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured.current(), 1, s, info);
   } else if constexpr (WarpPlan<T, LA, LB, LC, LD>::fits) {
     // Both kernels serve these classes and the autotuner picks one.  Variant 0
     // is the warp kernel in FP64 and the cooperative one in FP32, the faster
@@ -1051,18 +1064,18 @@ cudaError_t launch_one(const JKLaunch& a, int grid, int variant, cudaStream_t s,
     using C = CoopPlan<T, LA, LB, LC, LD>;
     constexpr bool warp_first = sizeof(T) == 8;
     if ((variant == 0) == warp_first) {
-      static bool configured = false;
-      return start(k_jk_warp<T, LA, LB, LC, LD>, a, grid, 32 * W::WARPS, W::SMEM, configured, 2, s, info);
+      static PerDeviceFlag configured;
+      return start(k_jk_warp<T, LA, LB, LC, LD>, a, grid, 32 * W::WARPS, W::SMEM, configured.current(), 2, s, info);
     }
-    static bool configured = false;
-    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured, 2, s, info);
+    static PerDeviceFlag configured;
+    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), 2, s, info);
   } else if constexpr (CoopPlan<T, LA, LB, LC, LD>::fits) {
     using C = CoopPlan<T, LA, LB, LC, LD>;
-    static bool configured = false;
-    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured, 1, s, info);
+    static PerDeviceFlag configured;
+    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), 1, s, info);
   } else {
-    static bool configured = false;
-    return start(k_jk_generic<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured, 1, s, info);
+    static PerDeviceFlag configured;
+    return start(k_jk_generic<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured.current(), 1, s, info);
   }
 }
 #endif

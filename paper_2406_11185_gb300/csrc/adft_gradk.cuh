@@ -303,7 +303,10 @@ cudaError_t launch_grad_one(const GradLaunch& g, int sms, cudaStream_t s);
 template <typename T, int LA, int LB, int LC, int LD, bool SWAP>
 static cudaError_t start_grad(const GradLaunch& g, int sms, cudaStream_t s) {
   using P = GradPlan<T, LA, LB, LC, LD>;
-  static int per_sm = 0;  // resident blocks per SM, queried once per instantiation
+  static int per_sm_dev[PerDeviceFlag::MAXDEV] = {};  // resident blocks per SM, per device
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= PerDeviceFlag::MAXDEV) dev = 0;
+  int& per_sm = per_sm_dev[dev];
   if (per_sm == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_grad_coop<T, LA, LB, LC, LD, SWAP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
