@@ -12,7 +12,15 @@ it, and the launch shape of every class-pair kernel is autotuned before
 timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                  [--precision fp64|mixed] [--impl reference]
+                  [--precision fp64|mixed] [--grad] [--impl reference]
+
+With N ranks (torchrun, one GPU each) the ranks share one molecule's build:
+rank 0 assigns the (band, class pair) launches to ranks by their autotuned
+times and broadcasts the partition, each rank evaluates its class pairs, and
+one sum all-reduce of the partial energy per step (of J and K in the
+end-to-end measurement) is the exchange; the value is one build's screened
+quartets over the slowest rank's time (strong scaling).  batch256 shards
+whole molecules across ranks instead.
 
 --impl reference times the CPU oracle (the plain FP64 reference written from
 the paper's definitions) on a bounded sample of the same workload.
@@ -309,9 +317,12 @@ def main():
 
     prec = args.precision
 
-    def step(p=prec):
-        return adft.adft_jk_energy(basis, D, thresh=thresh, split=split, precision=p, check=False,
-                                   on_device=True)
+    def step(p=prec, mask=None):
+        e = adft.adft_jk_energy(basis, D, thresh=thresh, split=split, precision=p, check=False,
+                                on_device=True, pair_mask=mask)
+        if mask is not None:  # this rank's class pairs: the sum over ranks is the energy
+            parallel.sum_partials(e)
+        return e
 
     def one_build(p):
         """(ms, energy, stats) of one build in precision p after autotuning it."""
@@ -330,12 +341,14 @@ def main():
     t0 = time.time()
     fp64_ms, E64, st64 = one_build("fp64")
     refs = {"fp64": {"s": fp64_ms / 1e3, "energy": E64}}
-    # autotune the timed precision (launch shape per class pair and band)
-    tune = adft.adft_autotune(basis, D, thresh=thresh, split=split, precision=prec)
+    # autotune the timed precision (launch shape per class pair and band); with
+    # several ranks the class pairs are shared out by their measured times
+    tune, tune_ms = adft.adft_autotune(basis, D, thresh=thresh, split=split, precision=prec, return_times=True)
+    mask = parallel.class_pair_masks(tune_ms, ws, rank, device=dev) if ws > 1 else None
     tune_s = time.time() - t0
 
     for _ in range(args.warmup):
-        step()
+        step(prec, mask)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -345,7 +358,7 @@ def main():
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            e = step()
+            e = step(prec, mask)
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))
@@ -356,8 +369,9 @@ def main():
     Emix = float(e.item())
     st = adft.adft_jk_last_stats(basis)
     quartets = st["quartets_fp64"] + st["quartets_fp32"]
-    # slowest rank's time, all ranks' work (replicas: each rank builds the molecule)
-    ms_total, all_quartets = parallel.aggregate(float(sum(times)), quartets * args.steps, device=dev)
+    # slowest rank's time; the ranks share one molecule's build (class pairs
+    # sharded), so the work of all ranks together is one build per step
+    ms_total, all_quartets = parallel.aggregate(float(sum(times)), quartets * args.steps / ws, device=dev)
     ms = ms_total / args.steps
     value = all_quartets / (ms_total / 1e3)
 
@@ -372,7 +386,10 @@ def main():
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         Dd.copy_(Dh, non_blocking=True)
-        adft.adft_jk_build(basis, Dd, thresh=thresh, split=split, precision=prec, check=True, out=(Jd, Kd))
+        adft.adft_jk_build(basis, Dd, thresh=thresh, split=split, precision=prec, check=True, out=(Jd, Kd),
+                           pair_mask=mask)
+        if mask is not None:
+            parallel.sum_partials(Jd, Kd)  # the exchange step: J and K summed over ranks
         Jh.copy_(Jd, non_blocking=True)
         Kh.copy_(Kd, non_blocking=True)
         b.record(stream)
@@ -394,14 +411,18 @@ def main():
             "other": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0,
                           "peak": v[2], "frac": ((v[1] / (v[0] / 1e3) / 1e12) / v[2]) if v[0] > 0 else 0.0}
                       for k, v in groups.items()}}
+    e2e_ms_max, _ = parallel.aggregate(float(np.mean(e2e_ms)), 0.0, device=dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "nbf": basis.nbf,
                        "natom": mol.natom, "nshell": mol.nshell, "thresh": thresh, "split": split,
                        "precision": prec, "l2": "flushed before every step (256 MB write)",
-                       "parallelism": f"replicas x{ws}", "launch_shapes": "autotuned per class pair"},
+                       "parallelism": ("single GPU" if ws == 1 else
+                                       f"class pairs sharded x{ws} (longest processing time on the measured "
+                                       "kernel times), one sum all-reduce of E per step (of J and K end to end)"),
+                       "launch_shapes": "autotuned per class pair"},
             "jk_build_s": ms / 1e3, "jk_build_s_fp64": fp64_ms / 1e3,
             "speedup_vs_fp64": fp64_ms / ms, "energy": Emix, "energy_fp64": E64,
             "energy_err_vs_fp64": abs(Emix - E64), "references": refs, "autotune_and_reference_s": tune_s,
@@ -411,16 +432,19 @@ def main():
                          "fp64_only_build": st64["quartets_fp64"]},
             "phases_ms": ph, "setup_s": setup_s,
             "clocks": clk.summary(),
-            "e2e": {"value": ws * quartets / (np.mean(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
-                    "d2h_bytes_per_step": 2 * nb2, "ms": float(np.mean(e2e_ms))},
+            "e2e": {"value": quartets / (e2e_ms_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
+                    "d2h_bytes_per_step": 2 * nb2, "ms": e2e_ms_max},
             "gpu_launches": None, "roofline": roof}
-    line["gpu_launches"] = launches_per_step(basis_classes(mol), mixed=prec == "mixed") * args.steps
+    line["gpu_launches"] = (launches_per_step(basis_classes(mol), mixed=prec == "mixed") if mask is None else
+                            5 + int(np.count_nonzero(mask))) * args.steps
     if args.grad:
         # one gradient of E_JK at the same D and options (untimed by the step loop)
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        g = adft.adft_jk_grad(basis, D, thresh=thresh, split=split, precision=prec, check=False)
+        g = adft.adft_jk_grad(basis, D, thresh=thresh, split=split, precision=prec, check=False, pair_mask=mask)
+        if mask is not None:
+            parallel.sum_partials(g)
         b.record(stream)
         b.synchronize()
         line["gradient"] = {"s": a.elapsed_time(b) / 1e3, "precision": prec,

@@ -98,6 +98,14 @@ typedef struct {
                       return ADFT_ERR_ASYM_D / ADFT_ERR_NONFINITE; 0: no check,
                       fully asynchronous */
   void* stream;    /* cudaStream_t, NULL = legacy default stream */
+  const unsigned char* pair_mask; /* host [2][55] or NULL (all): 1 = evaluate this
+                      (band, class pair) in this call, band-major (FP64, FP32),
+                      class pair X(X+1)/2 + Y.  With a mask, J, K, E and the
+                      gradient are partial sums: over calls (ranks) whose masks
+                      partition the class pairs they add up to the full result,
+                      so one sum all-reduce of J and K (or E, or the gradient) is
+                      the only exchange.  Single-molecule calls only (a batch is
+                      sharded by molecules). */
 } adft_opts;
 
 /* Per-call statistics of the last J/K build (host copies).  After a build

@@ -52,7 +52,7 @@ class adft_shell(ctypes.Structure):
 
 class adft_opts(ctypes.Structure):
     _fields_ = [("thresh", ctypes.c_double), ("split", ctypes.c_double), ("precision", ctypes.c_int),
-                ("check", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("check", ctypes.c_int), ("stream", ctypes.c_void_p), ("pair_mask", ctypes.c_void_p)]
 
 
 class adft_stats(ctypes.Structure):
@@ -129,10 +129,19 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def make_opts(thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None) -> adft_opts:
+def make_opts(thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None, pair_mask=None) -> adft_opts:
+    """adft_opts; pair_mask: None or [2, 55] of 0/1 (band, class pair) owned by
+    this call (the array is kept alive by the returned structure)."""
     prec = {"fp64": ADFT_PREC_FP64, "mixed": ADFT_PREC_MIXED}[precision] if isinstance(precision, str) \
         else int(precision)
-    return adft_opts(float(thresh), float(split), prec, 1 if check else 0, _stream_ptr(stream))
+    o = adft_opts(float(thresh), float(split), prec, 1 if check else 0, _stream_ptr(stream), None)
+    if pair_mask is not None:
+        m = np.ascontiguousarray(np.asarray(pair_mask, dtype=np.uint8).reshape(-1))
+        if m.size != 2 * NCP:
+            raise ValueError("pair_mask must hold 2 x 55 entries")
+        o.pair_mask = m.ctypes.data
+        o._mask = m
+    return o
 
 
 class Basis:
@@ -193,23 +202,26 @@ def _check_matrix(D, n):
         raise ValueError(f"D must be a contiguous CUDA float64 tensor of shape ({n}, {n})")
 
 
-def adft_jk_build(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None, out=None):
-    """J, K (torch CUDA float64) of Eq. 1 for density D."""
+def adft_jk_build(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None, out=None,
+                  pair_mask=None):
+    """J, K (torch CUDA float64) of Eq. 1 for density D (partial sums over the
+    class pairs of pair_mask, if given)."""
     import torch
     _check_matrix(D, basis.nbf)
     J, K = out if out is not None else (torch.empty_like(D), torch.empty_like(D))
-    o = make_opts(thresh, split, precision, check, stream)
+    o = make_opts(thresh, split, precision, check, stream, pair_mask)
     _check(load().adft_jk_build(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
                                 ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(K.data_ptr())), "adft_jk_build")
     return J, K
 
 
 def adft_jk_energy(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None,
-                   on_device=False):
-    """E_JK = 1/2 tr(DJ) - 1/4 tr(DK); a float, or a 1-element CUDA tensor."""
+                   on_device=False, pair_mask=None):
+    """E_JK = 1/2 tr(DJ) - 1/4 tr(DK); a float, or a 1-element CUDA tensor
+    (a partial sum over the class pairs of pair_mask, if given)."""
     import torch
     _check_matrix(D, basis.nbf)
-    o = make_opts(thresh, split, precision, check, stream)
+    o = make_opts(thresh, split, precision, check, stream, pair_mask)
     if on_device:
         E = torch.empty(1, dtype=torch.float64, device=D.device)
         _check(load().adft_jk_energy(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
@@ -221,12 +233,14 @@ def adft_jk_energy(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", 
     return e.value
 
 
-def adft_jk_grad(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None):
-    """dE_JK/dR [natom, 3] (torch CUDA float64) at fixed D."""
+def adft_jk_grad(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None,
+                 pair_mask=None):
+    """dE_JK/dR [natom, 3] (torch CUDA float64) at fixed D (a partial sum over
+    the class pairs of pair_mask, if given)."""
     import torch
     _check_matrix(D, basis.nbf)
     g = torch.empty((basis.natom, 3), dtype=torch.float64, device=D.device)
-    o = make_opts(thresh, split, precision, check, stream)
+    o = make_opts(thresh, split, precision, check, stream, pair_mask)
     _check(load().adft_jk_grad(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
                                ctypes.c_void_p(g.data_ptr())), "adft_jk_grad")
     return g

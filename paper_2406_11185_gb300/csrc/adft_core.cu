@@ -742,6 +742,7 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
         const int nY = b->cls_first[Y + 1] - b->cls_first[Y];
         if (nX == 0 || nY == 0) continue;
         const int cp = cp_index(X, Y);
+        if (o->pair_mask && !o->pair_mask[band * NCP + cp]) continue;  // another rank's share
         L.bra_first = b->cls_first[X]; L.nbra = nX; L.ket_first = b->cls_first[Y];
         L.same_class = (X == Y);
         L.prefix = (band ? w.pre32 : w.pre64) + b->pre_off[cp];
@@ -1512,6 +1513,7 @@ int adft_batch_jk(adft_batch* bt, const double* D, const adft_opts* o, double* J
   int st = call_begin(b, D, o);
   if (st) return st;
   if (!J || !K) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  if (o->pair_mask) { set_error("pair_mask is for single-molecule calls; shard a batch by molecules"); return ADFT_ERR_ARG; }
   cudaStream_t s = (cudaStream_t)o->stream;
   if (o->check || s == nullptr) {
     // direct launches (validation needs a synchronisation; the legacy
