@@ -369,6 +369,15 @@ def main():
     Emix = float(e.item())
     st = adft.adft_jk_last_stats(basis)
     quartets = st["quartets_fp64"] + st["quartets_fp32"]
+    # primitive quartets evaluated by all ranks together (each rank's kernels count their own)
+    _, prim_all = parallel.aggregate(0.0, float(st["prim_quartets_fp64"] + st["prim_quartets_fp32"]), device=dev)
+    # Cartesian integrals of the kept quartets (per class pair, from one screening pass)
+    try:
+        _, q_cp = adft.adft_jk_plan(basis, D, thresh=thresh, split=split, precision=prec)
+        cart_eris = float(np.sum(q_cp * cartesian_block_sizes()[None, :]))
+    except Exception as exc:  # an auxiliary figure: never lose the bench line over it
+        cart_eris = None
+        print(f"bench: Cartesian ERI count unavailable: {exc}", file=sys.stderr)
     # slowest rank's time; the ranks share one molecule's build (class pairs
     # sharded), so the work of all ranks together is one build per step
     ms_total, all_quartets = parallel.aggregate(float(sum(times)), quartets * args.steps / ws, device=dev)
@@ -430,6 +439,9 @@ def main():
                          "unique_before_screening": st["quartets_total"],
                          "prim_fp64_band": st["prim_quartets_fp64"], "prim_fp32_band": st["prim_quartets_fp32"],
                          "fp64_only_build": st64["quartets_fp64"]},
+            "throughput": {"screened_quartets_per_s": value,
+                           "cartesian_eris_per_s": None if cart_eris is None else cart_eris / (ms / 1e3),
+                           "primitive_quartets_per_s": prim_all / (ms / 1e3)},
             "phases_ms": ph, "setup_s": setup_s,
             "clocks": clk.summary(),
             "e2e": {"value": quartets / (e2e_ms_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
@@ -469,6 +481,14 @@ def basis_classes(mol):
             if a >= b:
                 present.add((a, b))
     return len(present)
+
+
+def cartesian_block_sizes():
+    """Cartesian integrals per shell quartet of every class pair X(X+1)/2 + Y,
+    class X = l_a(l_a+1)/2 + l_b (l_a >= l_b, l <= 3): [55]."""
+    nc = [(l + 1) * (l + 2) // 2 for l in range(4)]
+    cls = [nc[la] * nc[lb] for la in range(4) for lb in range(la + 1)]
+    return np.array([cls[x] * cls[y] for x in range(len(cls)) for y in range(x + 1)], dtype=np.float64)
 
 
 def launches_per_step(ncls, mixed=True):
