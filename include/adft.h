@@ -125,8 +125,8 @@ typedef struct {
 
 /* Create a basis on the current CUDA device: copies the geometry and shells,
  * builds the shell-pair data (Gaussian product centres, exponents and
- * prefactors of every primitive pair, Sec. 1.2.2 "basis contractions ... as
- * different shells": every shell is one segmented contraction), evaluates the
+ * prefactors of every primitive pair; as in Sec. 1.2.2, each contraction of a
+ * given angular momentum is its own shell, i.e. a segmented contraction), evaluates the
  * Schwarz bounds Q_ab on the GPU and sorts the pairs of each
  * angular-momentum class (l_a >= l_b) by descending Q (the angular-momentum
  * reordering of Sec. 1.2.2).  Primitive pairs whose bound Q_p times the

@@ -1,12 +1,13 @@
 // Group-cooperative J/K kernel for the larger angular-momentum classes.
 //
-// A group of GS lanes (GS = number of ket Cartesian components, at most 32)
-// owns one shell quartet.  Lane gl owns ket components gl, gl+GS, ...; for
+// A group of GS lanes owns one shell quartet (GS and SLOTS are chosen together
+// by coop_shape below).  Lane gl owns ket components gl, gl+GS, ...; for
 // every bra primitive p the group evaluates the Hermite integrals R of up to
 // SLOTS ket primitives at once (one ket primitive per lane, written to shared
 // memory together with that primitive's ket Hermite expansion coefficients),
 // then every lane applies the ket transform of its own components to all of
-// them:  W_p[tuv][cd] += sum_{tau nu phi} (+-) E^cd_{tau nu phi} R_{t+tau,u+nu,v+phi}.
+// them:  W_p[tuv][cd] += sum_{tau nu phi} (+-) E^cd_{tau nu phi} R_{t+tau,u+nu,v+phi},
+// one flat loop over each component's (tau, nu, phi) terms (KetTermTable).
 // The bra transform of W_p is accumulated into the contracted block in
 // shared memory, and the J/K digestion reads that block.  Compared with one
 // thread per quartet this computes R once per primitive quartet instead of

@@ -1,9 +1,9 @@
 // Device templates of the per-class ERI kernels (McMurchie-Davidson) with the
 // J/K digestion fused in.  Included by the per-precision translation units,
 // which instantiate one kernel per angular-momentum class pair
-// (la lb | lc ld), la >= lb, lc >= ld, (la,lb) >= (lc,ld): the
-// per-angular-momentum code paths of Sec. 1.2.2 ("GPU kernel code optimized
-// for each type of angular momentum"), generated here by the C++ compiler from
+// (la lb | lc ld), la >= lb, lc >= ld, (la,lb) >= (lc,ld).  Sec. 1.2.2 gives
+// every angular-momentum combination its own generated code path, since their
+// recurrence graphs differ; here the C++ compiler generates those paths from
 // one template instead of a separate code generator.
 //
 // Integral scheme (Helgaker, Jorgensen, Olsen, "Molecular Electronic-Structure
