@@ -277,7 +277,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=os.environ.get("ADFT_BENCH_WORKLOAD", "c60"), choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="adft", choices=["adft", "reference"])
@@ -442,6 +442,8 @@ def main():
             "throughput": {"screened_quartets_per_s": value,
                            "cartesian_eris_per_s": None if cart_eris is None else cart_eris / (ms / 1e3),
                            "primitive_quartets_per_s": prim_all / (ms / 1e3)},
+            "step_ms": {"mean": ms, "median": float(np.median(times)), "min": float(np.min(times)),
+                        "max": float(np.max(times))},
             "phases_ms": ph, "setup_s": setup_s,
             "clocks": clk.summary(),
             "e2e": {"value": quartets / (e2e_ms_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
