@@ -99,3 +99,32 @@ def test_autograd_function_available_without_gpu():
     torch = pytest.importorskip("torch")
     assert issubclass(adft.JKEnergy, torch.autograd.Function)
     assert adft._jk_energy_function() is adft.JKEnergy
+
+
+def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
+    """The boundary is a C ABI: the header compiles as C11 with every warning
+    on, and a C program links against the library and calls the entry points
+    that need no GPU."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_adft.c"
+    src.write_text(
+        '#include "adft.h"\n#include <stdio.h>\n#include <string.h>\n'
+        "int main(void) {\n"
+        "  adft_basis* b = 0;\n"
+        "  if (adft_basis_create(0, 0, 0, 0, 1, &b) != ADFT_ERR_ARG || b) return 2;\n"
+        "  if (strlen(adft_last_error_message()) == 0) return 3;\n"
+        "  printf(\"%s|%s\\n\", adft_version(), adft_status_string(ADFT_ERR_ARG));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "use_adft"
+    libdir = os.path.dirname(adft.LIB_PATH)
+    cmd = [gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           str(src), "-o", str(exe), "-L", libdir, "-ladft", f"-Wl,-rpath,{libdir}"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    version, msg = out.stdout.strip().split("|")
+    assert version.startswith("adft") and len(msg) > 0
