@@ -7,12 +7,14 @@ precision bands, the spherical transforms and the energy E_JK
 (adft_jk_energy), with the basis (pairs and Schwarz bounds) built once before
 timing, as in an SCF loop.  The metric is screened shell quartets per second
 of the mixed-precision build (--precision mixed: FP64 band in native FP64,
-FP32 band in FP32); the plain FP64 build of the same molecule is timed beside
-it, and the launch shape of every class-pair kernel is autotuned before
-timing.
+FP32 band in FP32) on the 2,064-function molecule (the "~2k basis functions"
+point); the plain FP64 build of the same molecule is timed after it, and the
+60-atom molecule's mixed and FP64 builds are reported beside it.  Launch
+shapes are autotuned per class pair on the 60-atom molecule of the same
+recipe and installed before timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                  [--precision fp64|mixed] [--grad] [--impl reference]
+                  [--precision fp64|mixed] [--split S] [--grad] [--impl reference]
 
 With N ranks (torchrun, one GPU each) the ranks share one molecule's build:
 rank 0 assigns the (band, class pair) launches to ranks by their autotuned
@@ -43,12 +45,14 @@ sys.path.insert(0, ROOT)
 METRIC = "J+K build sec & screened quartets/s at ~2k basis fns; mixed vs FP64 at 1e-6 Eh"
 UNIT = "screened quartets/s"
 WORKLOADS = {
+    "c240": "96 heavy (3s2p1d) + 144 H (2s1p) atoms, 1-6 primitives, exponents 0.1-5e3, "
+            "2064 spherical functions, thresh 1e-10, mixed FP32/FP64 (the ~2k-function point)",
     "c120": "48 heavy (4s3p2d1f) + 72 H (3s2p1d) atoms, 1-8 primitives, exponents 0.05-1e4, "
             "2448 spherical functions, thresh 1e-12, split 1e-5, mixed FP32/FP64",
     "c200": "80 heavy (4s3p2d1f) + 120 H (3s2p1d) atoms, 1-8 primitives, exponents 0.05-1e4, "
             "4080 spherical functions, thresh 1e-12, split 1e-5, mixed FP32/FP64",
     "c60": "24 heavy (3s2p1d) + 36 H (2s1p) atoms, 1-6 primitives, exponents 0.1-5e3, "
-           "516 spherical functions, thresh 1e-10, split 1e-5, mixed FP32/FP64",
+           "516 spherical functions, thresh 1e-10, mixed FP32/FP64",
     "small": "3 heavy (3s2p1d) + 5 H (2s1p) atoms, 1-6 primitives, exponents 0.1-5e3, "
              "67 spherical functions, thresh 1e-10, split 1e-5, mixed FP32/FP64 (profiling case)",
     "batch256": "256 molecules of 10-40 atoms (40 % heavy, 3s2p1d / 2s1p, 1-6 primitives), 86-344 "
@@ -56,12 +60,6 @@ WORKLOADS = {
                 "molecule in one batched, graph-captured call per step; thresh 1e-10, split 1e-5, "
                 "mixed FP32/FP64",
 }
-# Peaks of plain ALU arithmetic derived from unit counts and the maximum
-# clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz, and the FP64 rate of
-# 2 FMA per SM per clock (1.26 TFLOP/s, the 1.25 TFLOP/s nominal figure).
-SMS, CLK_MAX = 152, 2.07e9
-PEAK_FP32 = SMS * 128 * 2 * CLK_MAX / 1e12
-PEAK_FP64 = SMS * 2 * 2 * CLK_MAX / 1e12
 
 
 def _dist():
@@ -274,16 +272,78 @@ def run_reference(args):
     return 0
 
 
+def one_phase(basis, D, stream, flush, kw, steps, warmup, mask=None, sampler=None):
+    """Per-step device times (ms) of adft_jk_energy builds: `warmup` untimed
+    builds, then `steps` timed ones, each after an L2 flush, with CUDA events
+    on the launching stream.  Returns (times, phases, energy tensor)."""
+    import torch
+    from paper_2406_11185_gb300 import adft, parallel
+
+    def step():
+        e = adft.adft_jk_energy(basis, D, check=False, on_device=True, pair_mask=mask, **kw)
+        if mask is not None:  # this rank's class pairs: the sum over ranks is the energy
+            parallel.sum_partials(e)
+        return e
+
+    e = None
+    for _ in range(warmup):
+        e = step()
+    torch.cuda.synchronize()
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    times, phases = [], []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e = step()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        phases.append(adft.adft_jk_last_timings(basis))
+    torch.cuda.synchronize()
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    return times, phases, e
+
+
+def stored_blocks(name):
+    """The oracle's sampled J/K blocks of a workload (tests/golden/<name>_blocks.json,
+    written by tests/golden/make_golden.py), or None."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_blocks.json")
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
+def blocks_error(mol, J, K, ref):
+    """max |dJ|, |dK| over the stored oracle blocks."""
+    o, sl = 0, []
+    for _, l, _, _ in mol.shells:
+        n = 2 * l + 1 if mol.spherical else (l + 1) * (l + 2) // 2
+        sl.append(slice(o, o + n))
+        o += n
+    Jc, Kc = J.cpu().numpy(), K.cpu().numpy()
+    ej = max(float(np.max(np.abs(Jc[sl[a], sl[b]] - np.array(Jb)))) for (a, b), Jb in zip(ref["pairs"], ref["J"]))
+    ek = max(float(np.max(np.abs(Kc[sl[a], sl[b]] - np.array(Kb)))) for (a, b), Kb in zip(ref["pairs"], ref["K"]))
+    return {"max_abs_dJ": ej, "max_abs_dK": ek, "blocks": len(ref["pairs"])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=os.environ.get("ADFT_BENCH_WORKLOAD", "c60"), choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=os.environ.get("ADFT_BENCH_WORKLOAD", "c240"), choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="adft", choices=["adft", "reference"])
     ap.add_argument("--ref-budget", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--split", type=float, default=None, help="FP64 band iff Q_ab Q_cd >= split (default: the "
+                    "workload's)")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed builds of the plain FP64 arm (default: --steps on the 60-atom molecule, 1 on "
+                         "the 2,064-function one, whose FP64 build takes minutes)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 60-atom mixed and FP64 arms reported beside a larger workload")
     ap.add_argument("--compare-loop", action="store_true",
                     help="batch256: also time the same work as a loop of single-molecule calls")
     ap.add_argument("--grad", action="store_true",
@@ -305,98 +365,71 @@ def main():
     torch.cuda.set_device(dev)
     from paper_2406_11185_gb300 import adft, parallel
 
-    mol, opt, Dn = workload(args.workload)
     t0 = time.time()
+    mol, opt, Dn = workload(args.workload)
     basis = adft.Basis.from_molecule(mol)
     torch.cuda.synchronize()
     setup_s = time.time() - t0
     D = torch.from_numpy(Dn).to(dev)
-    thresh, split = opt["thresh"], opt["split"]
+    thresh = opt["thresh"]
+    split = opt["split"] if args.split is None else args.split
+    prec = args.precision
+    kw = dict(thresh=thresh, split=split, precision=prec)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    prec = args.precision
+    # measured ALU peaks of this GPU (the roofline denominators)
+    peaks = {"fp64": adft.adft_alu_peak(True, 4000), "fp32": adft.adft_alu_peak(False, 20000)}
 
-    def step(p=prec, mask=None):
-        e = adft.adft_jk_energy(basis, D, thresh=thresh, split=split, precision=p, check=False,
-                                on_device=True, pair_mask=mask)
-        if mask is not None:  # this rank's class pairs: the sum over ranks is the energy
-            parallel.sum_partials(e)
-        return e
-
-    def one_build(p):
-        """(ms, energy, stats) of one build in precision p after autotuning it."""
-        adft.adft_autotune(basis, D, thresh=thresh, split=split, precision=p)
-        step(p)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.zero_()
-        a.record(stream)
-        e = step(p)
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b), float(e.item()), adft.adft_jk_last_stats(basis)
-
-    # reference builds on the same GPU: plain FP64 and (if different) native mixed
+    # launch shapes: autotuned on the 60-atom molecule of the same recipe (its
+    # kernels cover the same class pairs in seconds) and installed here
     t0 = time.time()
-    fp64_ms, E64, st64 = one_build("fp64")
-    refs = {"fp64": {"s": fp64_ms / 1e3, "energy": E64}}
-    # autotune the timed precision (launch shape per class pair and band); with
-    # several ranks the class pairs are shared out by their measured times
-    tune, tune_ms = adft.adft_autotune(basis, D, thresh=thresh, split=split, precision=prec, return_times=True)
-    mask = parallel.class_pair_masks(tune_ms, ws, rank, device=dev) if ws > 1 else None
+    tune_name = "c60" if args.workload == "c240" else args.workload
+    if tune_name != args.workload:
+        tmol, topt, tD = workload(tune_name)
+        tbasis = adft.Basis.from_molecule(tmol)
+        tDt = torch.from_numpy(tD).to(dev)
+    else:
+        tmol, topt, tbasis, tDt = mol, opt, basis, D
+    tab64, ms64 = adft.adft_autotune(tbasis, tDt, thresh=topt["thresh"], precision="fp64", return_times=True)
+    tab, tune_ms = adft.adft_autotune(tbasis, tDt, thresh=topt["thresh"], split=split, precision=prec,
+                                      return_times=True)
+    adft.adft_set_tuning(basis, tab)
     tune_s = time.time() - t0
+    mask = parallel.class_pair_masks(tune_ms, ws, rank, device=dev) if ws > 1 else None
 
-    for _ in range(args.warmup):
-        step(prec, mask)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    times, phases = [], []
+    # ---- the timed arm (the metric): K steps after W warm-up steps
     with ClockSampler(dev.index or 0) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            e = step(prec, mask)
-            b.record(stream)
-            b.synchronize()
-            times.append(a.elapsed_time(b))
-            phases.append(adft.adft_jk_last_timings(basis))
-        torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    Emix = float(e.item())
+        times, phases, e = one_phase(basis, D, stream, flush, kw, args.steps, args.warmup, mask)
+    Emain = float(e.item())
     st = adft.adft_jk_last_stats(basis)
+    cls = adft.adft_jk_last_class_stats(basis)
     quartets = st["quartets_fp64"] + st["quartets_fp32"]
-    # primitive quartets evaluated by all ranks together (each rank's kernels count their own)
     _, prim_all = parallel.aggregate(0.0, float(st["prim_quartets_fp64"] + st["prim_quartets_fp32"]), device=dev)
-    # Cartesian integrals of the kept quartets (per class pair, from one screening pass)
-    try:
-        _, q_cp = adft.adft_jk_plan(basis, D, thresh=thresh, split=split, precision=prec)
-        cart_eris = float(np.sum(q_cp * cartesian_block_sizes()[None, :]))
-    except Exception as exc:  # an auxiliary figure: never lose the bench line over it
-        cart_eris = None
-        print(f"bench: Cartesian ERI count unavailable: {exc}", file=sys.stderr)
-    # slowest rank's time; the ranks share one molecule's build (class pairs
-    # sharded), so the work of all ranks together is one build per step
+    cart_eris = float(np.sum(cls["quartets"] * cartesian_block_sizes()[None, :]))
     ms_total, all_quartets = parallel.aggregate(float(sum(times)), quartets * args.steps / ws, device=dev)
     ms = ms_total / args.steps
     value = all_quartets / (ms_total / 1e3)
+    ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
 
-    # end to end through the C ABI with host buffers: pinned D in, J and K out
+    # ---- accuracy of this build: stored oracle blocks (sampled J and K)
+    ref_blocks = stored_blocks(args.workload)
+    J, K = adft.adft_jk_build(basis, D, check=False, **kw)
+    acc = {"vs_oracle_blocks": blocks_error(mol, J, K, ref_blocks) if ref_blocks and mask is None else None}
+    del J, K
+
+    # ---- end to end through the C ABI with host buffers: pinned D in, J and K out
     Dh = torch.from_numpy(Dn).pin_memory()
     Jh = torch.empty_like(Dh).pin_memory()
     Kh = torch.empty_like(Dh).pin_memory()
     Jd, Kd, Dd = torch.empty_like(D), torch.empty_like(D), torch.empty_like(D)
     e2e_ms = []
-    for i in range(2):
+    for i in range(4):  # the first pass is a warm-up
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         Dd.copy_(Dh, non_blocking=True)
-        adft.adft_jk_build(basis, Dd, thresh=thresh, split=split, precision=prec, check=True, out=(Jd, Kd),
-                           pair_mask=mask)
+        adft.adft_jk_build(basis, Dd, check=False, out=(Jd, Kd), pair_mask=mask, **kw)
         if mask is not None:
             parallel.sum_partials(Jd, Kd)  # the exchange step: J and K summed over ranks
         Jh.copy_(Jd, non_blocking=True)
@@ -406,21 +439,40 @@ def main():
         if i > 0:
             e2e_ms.append(a.elapsed_time(b))
     nb2 = Dn.size * 8
+    e2e_ms_max, _ = parallel.aggregate(float(np.median(e2e_ms)), 0.0, device=dev)
 
-    # roofline of the dominant kernel group (ALU-bound ERI kernels)
-    ph = {k: float(np.mean([p[k] for p in phases])) for k in phases[0]}
-    groups = {"eri_fp32": (ph["eri_fp32_ms"], st["flops_fp32"], PEAK_FP32, "FP32 pipe"),
-              "eri_fp64": (ph["eri_fp64_ms"], st["flops_fp64"], PEAK_FP64, "FP64 pipe")}
+    # ---- the plain FP64 arm of the same molecule (mixed vs FP64 at the energy budget)
+    fp64_arm = None
+    if prec == "mixed":
+        n64 = args.fp64_steps if args.fp64_steps is not None else (1 if args.workload == "c240" else args.steps)
+        w64 = 0 if args.workload == "c240" else args.warmup  # FP64 kernels were warmed by the autotuner
+        if n64 > 0:
+            adft.adft_set_tuning(basis, tab64)
+            t64, ph64, e64 = one_phase(basis, D, stream, flush, dict(thresh=thresh, precision="fp64"), n64, w64,
+                                       mask)
+            E64 = float(e64.item())
+            fp64_arm = {"workload": args.workload, "steps": n64, "warmup": w64,
+                        "median_s": float(np.median(t64)) / 1e3, "min_s": float(np.min(t64)) / 1e3,
+                        "energy": E64, "energy_err_mixed_vs_fp64": abs(Emain - E64)}
+            if ref_blocks and mask is None:
+                J, K = adft.adft_jk_build(basis, D, check=False, thresh=thresh, precision="fp64")
+                fp64_arm["vs_oracle_blocks"] = blocks_error(mol, J, K, ref_blocks)
+                del J, K
+            adft.adft_set_tuning(basis, tab)
+
+    # ---- roofline of the dominant kernel group (the ALU-bound ERI kernels of a band)
+    groups = {"eri_fp32": (ph["eri_fp32_ms"], float(cls["flops"][1].sum()), peaks["fp32"]["tflops"], "FP32"),
+              "eri_fp64": (ph["eri_fp64_ms"], float(cls["flops"][0].sum()), peaks["fp64"]["tflops"], "FP64")}
     dom = max(groups, key=lambda k: groups[k][0])
     gms, gfl, gpk, gkind = groups[dom]
     ach = gfl / (gms / 1e3) / 1e12 if gms > 0 else 0.0
     roof = {"bound": "alu", "kernel": f"{dom} (all class-pair launches of the band)", "achieved": ach,
-            "peak": gpk, "unit": "TFLOP/s", "frac": ach / gpk, "traffic": None,
-            "peak_kind": f"derived: 152 SMs x 2.07 GHz, {gkind}",
+            "peak": gpk, "unit": "TFLOP/s", "frac": ach / gpk if gpk else None, "traffic": None,
+            "peak_kind": f"measured in this run: adft_alu_peak ({gkind} FMA chains on every SM)",
+            "flops_model": "class_flops per evaluated primitive quartet, bra primitive and quartet",
             "other": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0,
-                          "peak": v[2], "frac": ((v[1] / (v[0] / 1e3) / 1e12) / v[2]) if v[0] > 0 else 0.0}
+                          "peak": v[2], "frac": ((v[1] / (v[0] / 1e3) / 1e12) / v[2]) if v[0] > 0 and v[2] else 0.0}
                       for k, v in groups.items()}}
-    e2e_ms_max, _ = parallel.aggregate(float(np.mean(e2e_ms)), 0.0, device=dev)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32+f64" if prec == "mixed" else "f64",
@@ -431,32 +483,56 @@ def main():
                        "parallelism": ("single GPU" if ws == 1 else
                                        f"class pairs sharded x{ws} (longest processing time on the measured "
                                        "kernel times), one sum all-reduce of E per step (of J and K end to end)"),
-                       "launch_shapes": "autotuned per class pair"},
-            "jk_build_s": ms / 1e3, "jk_build_s_fp64": fp64_ms / 1e3,
-            "speedup_vs_fp64": fp64_ms / ms, "energy": Emix, "energy_fp64": E64,
-            "energy_err_vs_fp64": abs(Emix - E64), "references": refs, "autotune_and_reference_s": tune_s,
+                       "launch_shapes": f"autotuned per class pair on {tune_name}"},
+            "jk_build_s": ms / 1e3, "jk_build_s_fp64": None if fp64_arm is None else fp64_arm["median_s"],
+            "speedup_vs_fp64": None if fp64_arm is None else fp64_arm["median_s"] * 1e3 / ms,
+            "energy": Emain, "energy_fp64": None if fp64_arm is None else fp64_arm["energy"],
+            "energy_err_vs_fp64": None if fp64_arm is None else fp64_arm["energy_err_mixed_vs_fp64"],
+            "fp64_arm": fp64_arm, "accuracy": acc, "autotune_s": tune_s,
             "quartets": {"fp64_band": st["quartets_fp64"], "fp32_band": st["quartets_fp32"],
                          "unique_before_screening": st["quartets_total"],
-                         "prim_fp64_band": st["prim_quartets_fp64"], "prim_fp32_band": st["prim_quartets_fp32"],
-                         "fp64_only_build": st64["quartets_fp64"]},
-            "throughput": {"screened_quartets_per_s": value,
-                           "cartesian_eris_per_s": None if cart_eris is None else cart_eris / (ms / 1e3),
+                         "prim_fp64_band": st["prim_quartets_fp64"], "prim_fp32_band": st["prim_quartets_fp32"]},
+            "throughput": {"screened_quartets_per_s": value, "cartesian_eris_per_s": cart_eris / (ms / 1e3),
                            "primitive_quartets_per_s": prim_all / (ms / 1e3)},
             "step_ms": {"mean": ms, "median": float(np.median(times)), "min": float(np.min(times)),
                         "max": float(np.max(times))},
-            "phases_ms": ph, "setup_s": setup_s,
+            "phases_ms": ph, "setup_s": setup_s, "peaks": peaks,
             "clocks": clk.summary(),
             "e2e": {"value": quartets / (e2e_ms_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": nb2,
-                    "d2h_bytes_per_step": 2 * nb2, "ms": e2e_ms_max},
-            "gpu_launches": None, "roofline": roof}
-    line["gpu_launches"] = (launches_per_step(basis_classes(mol), mixed=prec == "mixed") if mask is None else
-                            5 + int(np.count_nonzero(mask))) * args.steps
+                    "d2h_bytes_per_step": 2 * nb2, "ms": e2e_ms_max, "samples": len(e2e_ms)},
+            "gpu_launches": (launches_per_step(basis_classes(mol), mixed=prec == "mixed") if mask is None else
+                             5 + int(np.count_nonzero(mask))) * args.steps,
+            "roofline": roof}
+
+    # ---- the 60-atom molecule beside a larger workload: mixed and FP64 arms
+    # with the same steps and warm-up (both medians)
+    if args.workload != "c60" and not args.no_secondary and mask is None and prec == "mixed":
+        smol, sopt, sDn = workload("c60")
+        sb = tbasis if tune_name == "c60" else adft.Basis.from_molecule(smol)
+        sD = torch.from_numpy(sDn).to(dev)
+        skw = dict(thresh=sopt["thresh"], split=split, precision="mixed")
+        adft.adft_set_tuning(sb, tab)
+        tm, _, em = one_phase(sb, sD, stream, flush, skw, args.steps, args.warmup)
+        adft.adft_set_tuning(sb, tab64)
+        t64, _, e64 = one_phase(sb, sD, stream, flush, dict(thresh=sopt["thresh"], precision="fp64"), args.steps,
+                                args.warmup)
+        ssts = adft.adft_jk_last_stats(sb)
+        q = ssts["quartets_fp64"] + ssts["quartets_fp32"]
+        Jm, Km = adft.adft_jk_build(sb, sD, check=False, **skw)
+        sref = stored_blocks("c60")
+        line["c60"] = {"workload": f"c60: {WORKLOADS['c60']}", "split": split, "steps": args.steps,
+                       "warmup": args.warmup, "mixed_median_s": float(np.median(tm)) / 1e3,
+                       "fp64_median_s": float(np.median(t64)) / 1e3,
+                       "speedup_vs_fp64": float(np.median(t64)) / float(np.median(tm)),
+                       "screened_quartets_per_s": q / (float(np.median(tm)) / 1e3),
+                       "energy_err_mixed_vs_fp64": abs(float(em.item()) - float(e64.item())),
+                       "mixed_vs_oracle_blocks": blocks_error(smol, Jm, Km, sref) if sref else None}
     if args.grad:
-        # one gradient of E_JK at the same D and options (untimed by the step loop)
+        # one gradient of E_JK at the same D and options (outside the timed steps)
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        g = adft.adft_jk_grad(basis, D, thresh=thresh, split=split, precision=prec, check=False, pair_mask=mask)
+        g = adft.adft_jk_grad(basis, D, check=False, pair_mask=mask, **kw)
         if mask is not None:
             parallel.sum_partials(g)
         b.record(stream)

@@ -167,9 +167,29 @@ int adft_jk_energy(adft_basis* b, const double* D, const adft_opts* opts, double
  *   grad: dev [natom*3] float64, overwritten. */
 int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* opts, double* grad);
 
+/* One-electron matrices of the core Hamiltonian H = T + V that the Fock
+ * matrix of Eq. 1 adds to J and K (the SCF driver around the J/K build):
+ * overlap S, kinetic energy T and nuclear attraction
+ * V_mn = -sum_C Z_C <m| 1/|r - R_C| |n>, in the basis's functions (spherical
+ * or Cartesian as created).  Single-molecule bases only.
+ *   charges: host [natom] nuclear charges Z_C (finite).
+ *   S, T, V: dev [nbf*nbf] row-major float64, overwritten.
+ *   stream: cudaStream_t or NULL.  Asynchronous (the charges are copied before
+ *   the call returns). */
+int adft_one_electron(adft_basis* b, const double* charges, void* stream, double* S, double* T, double* V);
+
 /* Statistics of the last adft_jk_build / adft_jk_energy / adft_jk_grad on
  * this handle (synchronises the handle's last stream). */
 int adft_jk_last_stats(adft_basis* b, adft_stats* st);
+
+/* Per class pair and band of the last adft_jk_build / adft_jk_energy (or
+ * adft_jk_plan: then only quartets): kept shell quartets, evaluated primitive
+ * quartets and bra primitives, and counted flops of the ERI + digestion kernel
+ * (the class's flop model applied to those counts).  Each output is host
+ * [2][55] (band-major: FP64 then FP32; class pair X(X+1)/2 + Y) or NULL.
+ * Synchronises the handle's last stream. */
+int adft_jk_last_class_stats(adft_basis* b, int64_t* quartets, int64_t* prim_quartets, int64_t* bra_prims,
+                             double* flops);
 
 /* Device time of the phases of the last adft_jk_build / adft_jk_energy /
  * adft_jk_grad on this handle, from CUDA events recorded on its stream
@@ -276,11 +296,30 @@ void adft_batch_destroy(adft_batch* bt);
  * shares it and keeps the last call's contents, and calls that overlap on the
  * GPU race on it (serialise them, e.g. on one stream).
  *   D, J, K: dev [nbf*nbf] row-major float64.  E: dev pointer to one float64.
+ *   All four must live on the current device, and the stream must belong to
+ *   it: the kernels run on the current device and dereference these pointers.
  *   nbf: 1..ADFT_STATIC_MAX_NBF, else ADFT_ERR_ARG.  stream: cudaStream_t or
  *   NULL.  Asynchronous.  The first call on each device looks up the device
  *   address of the scratch array (with that device current); make that first
- *   call before any stream capture. */
+ *   call before any stream capture.  With lazy module loading (the CUDA
+ *   default) that first lookup may load the library's device code, which
+ *   reserves device memory for the code and the array once per device; later
+ *   calls allocate nothing.  ADFT_ERR_CUDA reports a failed launch of this
+ *   call only (an error left by earlier work is not reported or cleared). */
 int adft_energy_static(const double* D, const double* J, const double* K, int nbf, double* E, void* stream);
+
+/* ---- measurement --------------------------------------------------------- */
+
+/* ALU peak of the current device for the roofline of the ERI kernels (which
+ * are bound by plain FP64 / FP32 arithmetic): a kernel of independent fused
+ * multiply-add chains on every SM, timed with CUDA events on the legacy
+ * default stream after one warm-up launch.  The paper has no counterpart; it
+ * is measurement support.
+ *   fp64: 1 = FP64 FMAs, 0 = FP32 FMAs.  iters: loop trips (each trip is 128
+ *   FMAs per thread; 2048 blocks of 256 threads on 152 SMs).
+ *   tflops: receives 2 x FMAs / time in TFLOP/s.  ms: the kernel time or NULL.
+ * Synchronous. */
+int adft_alu_peak(int fp64, int iters, double* tflops, double* ms);
 
 /* ---- utilities ---------------------------------------------------------- */
 

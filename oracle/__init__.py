@@ -57,6 +57,7 @@ def lib():
         L.orc_jk_blocks.argtypes = basis + [dp, ctypes.c_double, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int]
         L.orc_eri_tensor.argtypes = basis + [dp]
         L.orc_overlap.argtypes = basis + [dp]
+        L.orc_one_electron.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp]
         L.orc_grad.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, dp, dp, dp, ctypes.c_double, dp,
                                dp, ctypes.c_int]
         _lib = L
@@ -380,3 +381,80 @@ def energy_fd_grad(mol, D, thresh, h=1e-4, coords=None, nthreads=None):
             es.append(energy(D, J, K))
         out.append((es[0] - es[1]) / (2 * h))
     return np.array(out)
+
+
+# ----------------------------------------------------------------------------
+# SCF driver around the J/K build (the restricted closed-shell Fock iteration
+# of Eq. 1 with c_x = 1 and no exchange-correlation term, i.e. Hartree-Fock)
+
+
+def one_electron(mol, charges):
+    """Overlap S, kinetic T and nuclear attraction V in the molecule's basis
+    (the core Hamiltonian H = T + V of the Fock matrix of Eq. 1)."""
+    B = _Basis(mol)
+    q = np.ascontiguousarray(np.asarray(charges, dtype=np.float64))
+    S = np.zeros((B.nc, B.nc))
+    T = np.zeros((B.nc, B.nc))
+    V = np.zeros((B.nc, B.nc))
+    lib().orc_one_electron(*B.args(), mol.natom, _p(q), _p(S), _p(T), _p(V))
+    return _from_cart(mol, S), _from_cart(mol, T), _from_cart(mol, V)
+
+
+def nuclear_repulsion(mol, charges) -> float:
+    """sum_{A<B} Z_A Z_B / |R_A - R_B|."""
+    X = np.asarray(mol.atoms, dtype=np.float64)
+    Z = np.asarray(charges, dtype=np.float64)
+    e = 0.0
+    for a in range(len(Z)):
+        for b in range(a):
+            e += Z[a] * Z[b] / np.linalg.norm(X[a] - X[b])
+    return float(e)
+
+
+def scf(mol, charges, nocc, thresh, max_iter=100, e_tol=1e-10, g_tol=1e-8, diis_size=8):
+    """Restricted closed-shell SCF with the oracle's J and K, rebuilt in full
+    from the current density every iteration (no incremental builds):
+      F = H + J - 1/2 K,  E = 1/2 tr(D (H + F)) + E_nuc,  D = 2 C_occ C_occ^T,
+    C from the generalised eigenproblem F C = S C e (by S^(-1/2)), starting
+    from the core Hamiltonian, with Pulay DIIS on the error F D S - S D F.
+    Returns dict(energy, D, iterations, converged, F, S, H, e_nuc)."""
+    S, T, V = one_electron(mol, charges)
+    H = T + V
+    e_nuc = nuclear_repulsion(mol, charges)
+    s, U = np.linalg.eigh(S)
+    X = U @ np.diag(s ** -0.5) @ U.T
+
+    def density(F):
+        _, C = np.linalg.eigh(X.T @ F @ X)
+        C = X @ C[:, :nocc]
+        return 2.0 * C @ C.T
+
+    D = density(H)
+    Q = schwarz(mol)
+    focks, errs = [], []
+    E_old = None
+    for it in range(1, max_iter + 1):
+        J, K = jk(mol, D, thresh, Q=Q)
+        F = H + J - 0.5 * K
+        E = 0.5 * float(np.sum(D * (H + F))) + e_nuc
+        err = F @ D @ S - S @ D @ F
+        gnorm = float(np.max(np.abs(err)))
+        if E_old is not None and abs(E - E_old) < e_tol and gnorm < g_tol:
+            return dict(energy=E, D=D, iterations=it, converged=True, F=F, S=S, H=H, e_nuc=e_nuc)
+        E_old = E
+        focks.append(F)
+        errs.append(err)
+        focks, errs = focks[-diis_size:], errs[-diis_size:]
+        n = len(focks)
+        if n >= 2:
+            Bm = -np.ones((n + 1, n + 1))
+            Bm[n, n] = 0.0
+            for i in range(n):
+                for j in range(n):
+                    Bm[i, j] = float(np.sum(errs[i] * errs[j]))
+            rhs = np.zeros(n + 1)
+            rhs[n] = -1.0
+            c = np.linalg.solve(Bm, rhs)[:n]
+            F = sum(ci * Fi for ci, Fi in zip(c, focks))
+        D = density(F)
+    return dict(energy=E, D=D, iterations=max_iter, converged=False, F=F, S=S, H=H, e_nuc=e_nuc)

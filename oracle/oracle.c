@@ -707,3 +707,84 @@ void orc_grad(const double *xyz, int natom, int nshell, const int *atom, const i
   }
   free(off);
 }
+
+/* ------------------------------------------------------------------------ */
+/* One-electron integrals of the core Hamiltonian H = T + V used by the SCF
+   driver around the J/K build (Eq. 1: F = H + J - 1/2 c_x K, with H the
+   kinetic and nuclear-attraction terms).  Plain McMurchie-Davidson as in
+   Helgaker, Jorgensen and Olsen:
+     overlap, per direction      S_ij = E^{ij}_0 sqrt(pi/p)          (eq. 9.3.12)
+     kinetic, per direction      T_ij = -1/2 [ j(j-1) S_{i,j-2} - 2b(2j+1) S_{ij}
+                                              + 4 b^2 S_{i,j+2} ]     (from eq. 9.3.23:
+                                 the second derivative of the ket Gaussian)
+     T = Tx Sy Sz + Sx Ty Sz + Sx Sy Tz
+     nuclear attraction          V = - sum_C Z_C (2 pi / p)
+                                     sum_tuv E^{ij}_t E^{kl}_u E^{mn}_v R_tuv(p, P - C)   (eq. 9.9.32)
+   Outputs are full Cartesian [nc][nc] matrices (row-major). */
+void orc_one_electron(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
+                      const int *ptr, const double *exps, const double *coefs, int natom, const double *charges,
+                      double *S, double *T, double *V) {
+  orc_basis bs = {xyz, nshell, atom, l, nprim, ptr, exps, coefs};
+  int *off = (int *)malloc(sizeof(int) * (nshell + 1));
+  shell_offsets(&bs, off);
+  const int nc = off[nshell];
+  memset(S, 0, sizeof(double) * nc * nc);
+  memset(T, 0, sizeof(double) * nc * nc);
+  memset(V, 0, sizeof(double) * nc * nc);
+  for (int sa = 0; sa < nshell; ++sa)
+    for (int sb = 0; sb < nshell; ++sb) {
+      const int la = l[sa], lb = l[sb], na = ORC_NC(la), nb = ORC_NC(lb);
+      const double *A = xyz + 3 * atom[sa], *B = xyz + 3 * atom[sb];
+      int pa[3 * ORC_NC(ORC_LMAX)], pb[3 * ORC_NC(ORC_LMAX)];
+      cart_list(la, pa);
+      cart_list(lb, pb);
+      const int jm = lb + 2, nt = la + jm + 1;  /* E tables up to j = lb + 2 (kinetic) */
+      const int se = (la + 1) * (jm + 1) * nt;
+      for (int i = 0; i < nprim[sa]; ++i)
+        for (int j = 0; j < nprim[sb]; ++j) {
+          const double a = exps[ptr[sa] + i], b = exps[ptr[sb] + j], p = a + b;
+          const double cc = coefs[ptr[sa] + i] * prim_norm(a, la) * coefs[ptr[sb] + j] * prim_norm(b, lb);
+          double E[3 * (ORC_LMAX + 1) * (ORC_LMAX + 3) * (2 * ORC_LMAX + 3)];
+          for (int k = 0; k < 3; ++k) hermite_e(la, jm, a, b, A[k], B[k], E + k * se);
+#define EE(k, ii, jj, t) E[(k) * se + ((ii) * (jm + 1) + (jj)) * nt + (t)]
+          double P[3];
+          for (int k = 0; k < 3; ++k) P[k] = (a * A[k] + b * B[k]) / p;
+          const double sq = sqrt((double)ORC_PI / p);
+          const int L = la + lb;
+          double R[(2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1)];
+          for (int ia = 0; ia < na; ++ia)
+            for (int ib = 0; ib < nb; ++ib) {
+              const int *xa = pa + 3 * ia, *xb = pb + 3 * ib;
+              double s1[3], t1[3];
+              for (int k = 0; k < 3; ++k) {
+                const int ii = xa[k], jj = xb[k];
+                s1[k] = EE(k, ii, jj, 0) * sq;
+                const double sm2 = jj >= 2 ? EE(k, ii, jj - 2, 0) * sq : 0.0;
+                const double sp2 = EE(k, ii, jj + 2, 0) * sq;
+                t1[k] = -0.5 * (jj * (jj - 1) * sm2 - 2.0 * b * (2 * jj + 1) * s1[k] + 4.0 * b * b * sp2);
+              }
+              const long o = (long)(off[sa] + ia) * nc + off[sb] + ib;
+              S[o] += cc * s1[0] * s1[1] * s1[2];
+              T[o] += cc * (t1[0] * s1[1] * s1[2] + s1[0] * t1[1] * s1[2] + s1[0] * s1[1] * t1[2]);
+            }
+          for (int c = 0; c < natom; ++c) {
+            const double *C = xyz + 3 * c;
+            hermite_r(L, p, P[0] - C[0], P[1] - C[1], P[2] - C[2], R);
+            const double pref = -charges[c] * 2.0 * (double)ORC_PI / p;
+            for (int ia = 0; ia < na; ++ia)
+              for (int ib = 0; ib < nb; ++ib) {
+                const int *xa = pa + 3 * ia, *xb = pb + 3 * ib;
+                double s = 0.0;
+                for (int t = 0; t <= xa[0] + xb[0]; ++t)
+                  for (int u = 0; u <= xa[1] + xb[1]; ++u)
+                    for (int v = 0; v <= xa[2] + xb[2]; ++v)
+                      s += EE(0, xa[0], xb[0], t) * EE(1, xa[1], xb[1], u) * EE(2, xa[2], xb[2], v) *
+                           R[RIDX(t, u, v)];
+                V[(long)(off[sa] + ia) * nc + off[sb] + ib] += cc * pref * s;
+              }
+          }
+#undef EE
+        }
+    }
+  free(off);
+}

@@ -35,7 +35,7 @@ EXPORTED = [
     "adft_basis_destroy", "adft_batch_create", "adft_batch_offsets", "adft_batch_grad_offsets", "adft_batch_jk",
     "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version", "adft_autotune",
     "adft_set_tuning", "adft_jk_plan", "adft_energy_static", "adft_batch_last_stats", "adft_batch_last_timings", "adft_batch_autotune",
-    "adft_batch_set_tuning",
+    "adft_batch_set_tuning", "adft_alu_peak", "adft_jk_last_class_stats",
 ]
 
 
@@ -102,6 +102,9 @@ def load(path: str = LIB_PATH):
     L.adft_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(adft_opts), ctypes.POINTER(ctypes.c_int), dp]
     L.adft_batch_set_tuning.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.adft_energy_static.argtypes = [vp, vp, vp, ip, vp, vp]
+    L.adft_alu_peak.argtypes = [ip, ip, dp, dp]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.adft_jk_last_class_stats.argtypes = [vp, i64p, i64p, i64p, dp]
     L.adft_status_string.argtypes = [ip]
     L.adft_status_string.restype = ctypes.c_char_p
     L.adft_last_error_message.restype = ctypes.c_char_p
@@ -308,6 +311,20 @@ def adft_jk_last_stats(basis: Basis) -> dict:
     return {k: getattr(st, k) for k, _ in adft_stats._fields_}
 
 
+def adft_jk_last_class_stats(basis: Basis) -> dict:
+    """Per (band, class pair) arrays [2, 55]: quartets, prim_quartets,
+    bra_prims (int64) and flops (counted) of the last build."""
+    out = {k: np.zeros(2 * NCP, dtype=np.int64) for k in ("quartets", "prim_quartets", "bra_prims")}
+    fl = np.zeros(2 * NCP, dtype=np.float64)
+    i64 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _check(load().adft_jk_last_class_stats(basis.handle, i64(out["quartets"]), i64(out["prim_quartets"]),
+                                           i64(out["bra_prims"]), fl.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+           "adft_jk_last_class_stats")
+    res = {k: v.reshape(2, NCP) for k, v in out.items()}
+    res["flops"] = fl.reshape(2, NCP)
+    return res
+
+
 def adft_jk_last_timings(basis: Basis) -> dict:
     """Device milliseconds of the phases of the last call (CUDA events)."""
     ms = (ctypes.c_double * 4)()
@@ -455,6 +472,13 @@ def adft_batch_set_tuning(batch: Batch, table) -> None:
            "adft_batch_set_tuning")
 
 
+def adft_alu_peak(fp64: bool, iters: int = 20000) -> dict:
+    """Measured FMA peak of the current device: {"tflops", "ms"} (FP64 or FP32)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().adft_alu_peak(1 if fp64 else 0, int(iters), ctypes.byref(tf), ctypes.byref(ms)), "adft_alu_peak")
+    return {"tflops": tf.value, "ms": ms.value}
+
+
 def adft_energy_static(D, J, K, stream=None):
     """E = 1/2 tr(DJ) - 1/4 tr(DK) with no device allocation inside the call
     (scratch is a fixed array in the library); returns a 1-element CUDA
@@ -463,8 +487,13 @@ def adft_energy_static(D, J, K, stream=None):
     n = D.shape[0]
     for M in (D, J, K):
         _check_matrix(M, n)
-    E = torch.empty(1, dtype=torch.float64, device=D.device)
-    vp = ctypes.c_void_p
-    _check(load().adft_energy_static(vp(D.data_ptr()), vp(J.data_ptr()), vp(K.data_ptr()), n, vp(E.data_ptr()),
-                                     _stream_ptr(stream)), "adft_energy_static")
+        if M.device != D.device:
+            raise ValueError("D, J and K must be on the same CUDA device")
+    if stream is not None and getattr(stream, "device", D.device) != D.device:
+        raise ValueError("the stream must belong to D's device")
+    with torch.cuda.device(D.device):
+        E = torch.empty(1, dtype=torch.float64, device=D.device)
+        vp = ctypes.c_void_p
+        _check(load().adft_energy_static(vp(D.data_ptr()), vp(J.data_ptr()), vp(K.data_ptr()), n,
+                                         vp(E.data_ptr()), _stream_ptr(stream)), "adft_energy_static")
     return E

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 OUT = os.path.join(OUT_DIR, "libadft.so")
-SOURCES = ["adft_core.cu", "adft_dispatch.cu", "adft_grad.cu", "adft_static.cu"] + [
+SOURCES = ["adft_core.cu", "adft_dispatch.cu", "adft_grad.cu", "adft_static.cu", "adft_peaks.cu", "adft_onee.cu"] + [
     f"adft_eri{p}_{g}.cu" for p in ("64", "32") for g in ("a", "b", "c", "d", "e", "f", "g", "h")] + [
     f"adft_grad{p}_{g}.cu" for p in ("64", "32") for g in ("a", "b", "c")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -63,36 +63,6 @@ __device__ __forceinline__ void build_ket_terms(KetTermTable<LC, LD>& tab) {
   __syncthreads();
 }
 
-// In place Hermite integrals with compile-time L (same ordering argument as
-// hermite_R_rt: layer n overwrites layer n+1 by decreasing t+u+v).
-template <typename T, int L>
-__device__ __forceinline__ void hermite_R_inplace(const T* B, T X, T Y, T Z, T* R) {
-#pragma unroll
-  for (int n = L; n >= 0; --n)
-#pragma unroll
-    for (int s = L - n; s >= 0; --s)
-#pragma unroll
-      for (int t = s; t >= 0; --t)
-#pragma unroll
-        for (int u = s - t; u >= 0; --u) {
-          const int v = s - t - u;
-          T val;
-          if (s == 0) {
-            val = B[n];
-          } else if (t > 0) {
-            val = X * R[hidx(t - 1, u, v)];
-            if (t > 1) val += T(t - 1) * R[hidx(t - 2, u, v)];
-          } else if (u > 0) {
-            val = Y * R[hidx(t, u - 1, v)];
-            if (u > 1) val += T(u - 1) * R[hidx(t, u - 2, v)];
-          } else {
-            val = Z * R[hidx(t, u, v - 1)];
-            if (v > 1) val += T(v - 1) * R[hidx(t, u, v - 2)];
-          }
-          R[hidx(t, u, v)] = val;
-        }
-}
-
 // pref * R_tuv of one primitive quartet into R (any memory space)
 template <typename T, int L>
 __device__ __forceinline__ void prim_R_scaled(T alpha, T X, T Y, T Z, T pref, const BasisView& bv, T* R) {
@@ -104,14 +74,14 @@ __device__ __forceinline__ void prim_R_scaled(T alpha, T X, T Y, T Z, T pref, co
     T pw = pref;
 #pragma unroll
     for (int n = 0; n <= L; ++n) { B[n] *= pw; pw *= f; }
-    hermite_R_inplace<T, L>(B, X, Y, Z, R);
+    hermite_R<T, L>(B, X, Y, Z, R);
   } else {
     boys_fp32_scaled<L>(Tb, bv.boys32, B);
 #pragma unroll
     for (int n = 0; n <= L; ++n) B[n] *= (n & 1) ? -pref : pref;
     const float c = fmaxf(1.0f, 2.0f * Tb);
     const float s = sqrtf(2.0f * alpha / c);
-    hermite_R_inplace<T, L>(B, X * s, Y * s, Z * s, R);
+    hermite_R<T, L>(B, X * s, Y * s, Z * s, R);
     float sp = s;
 #pragma unroll
     for (int n = 1; n <= L; ++n) {
@@ -257,7 +227,7 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
   T* Gs = gbase + P::SLOTS * P::SLOT;   // [NAB][NCD] contracted block
   T* Eab = Gs + NAB * NCD;              // [3][EA] bra E of the current bra primitive
   const unsigned gmask = (GS == 32) ? 0xffffffffu : (((1u << GS) - 1u) << (g * GS));
-  const long long total = (long long)__ldg(a.prefix + a.nbra);
+  const long long total = (long long)__ldg(a.prefix + a.nseg);
   const BasisView& bv = a.bv;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
   const T* __restrict__ o2pa = Prec<T>::o2p(bv);

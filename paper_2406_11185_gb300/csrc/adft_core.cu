@@ -155,6 +155,7 @@ struct Workspace {
   int* status = nullptr;    // [4]: status word, abort flag
   double* scal = nullptr;   // [4]: energy, max|D|, max|D-D^T|
   double* Emol = nullptr;   // [nmol] energies
+  double* charges = nullptr;  // [natom] nuclear charges of a one-electron call
   unsigned long long* stats = nullptr;     // [10], see ScreenArgs::stats
   unsigned long long* work = nullptr;      // [2 bands][NCP][2] evaluated primitive quartets, bra primitives
 };
@@ -174,6 +175,9 @@ struct adft_basis {
   int npair = 0;
   int cls_first[adft::NCLS + 1];
   std::vector<int> seg_first;  // [NCLS][nmol+1]: first pair of class X of molecule m
+  // [(X * nmol + m) * NBK + k] (+1 end): first pair of contraction bucket k of
+  // class X, molecule m (pairs ordered by bucket, then descending Q)
+  std::vector<int> bseg_first;
   std::vector<int> pair_a, pair_b;
   std::vector<double> pair_Q;
   long long npp = 0, npp_dense = 0;
@@ -186,7 +190,7 @@ struct adft_basis {
   int *d_pair_a = nullptr, *d_pair_b = nullptr, *d_pair_ppoff = nullptr, *d_pair_ppn = nullptr, *d_pair_mol = nullptr;
   double *d_pair_Q = nullptr, *d_pair_AB = nullptr;
   long long* d_cumppn = nullptr;
-  int* d_seg_first = nullptr;
+  int* d_bseg_first = nullptr;
   int *d_mol_nc = nullptr, *d_mol_nbf = nullptr, *d_mol_cf_off = nullptr, *d_mol_f_off = nullptr;
   long long *d_mol_cbase = nullptr, *d_mol_obase = nullptr;
   adft::PrimPair<double>* d_pp64 = nullptr;
@@ -305,7 +309,7 @@ struct ScreenArgs {
   int cls_first[NCLS + 1];
   long long cnt_off[NCP];
   int nmol;
-  const int* seg_first;     // [NCLS][nmol+1]
+  const int* bseg_first;    // [(NCLS * nmol) * NBK + 1] bucketed segment starts
   const int* pair_mol;      // [npair] or NULL (one molecule)
   const double* Q;
   const int* ppn;
@@ -341,31 +345,33 @@ __global__ void k_screen(ScreenArgs a, int npair) {
     int X = 0;
     while (a.cls_first[X + 1] <= i) ++X;
     const int m = a.pair_mol ? a.pair_mol[i] : 0;
-    const int W = a.nmol + 1;
-    const int li = i - a.seg_first[X * W + m];  // index inside the molecule's class segment
     const double Qi = a.Q[i];
     const int nppi = a.ppn[i];
     for (int Y = 0; Y <= X; ++Y) {
-      const int f = a.seg_first[Y * W + m];
-      int n = a.seg_first[Y * W + m + 1] - f;
-      if (Y == X) n = li + 1;
-      const int keep = count_prefix(a.Q, f, n, Qi, a.thresh);
-      int n64 = keep;
-      if (a.mixed) n64 = min(keep, count_prefix(a.Q, f, n, Qi, a.split));
       const int cp = cp_index(X, Y);
-      const long long o = a.cnt_off[cp] + (i - a.cls_first[X]);
-      a.cnt64[o] = n64;
-      a.cnt32[o] = keep - n64;
-      a.kst64[o] = f - a.cls_first[Y];
-      a.kst32[o] = f - a.cls_first[Y] + n64;
-      q64 += n64; q32 += keep - n64; tot += n;
-      const unsigned long long s64 = a.cumppn[f + n64] - a.cumppn[f];
-      const unsigned long long s32 = a.cumppn[f + keep] - a.cumppn[f + n64];
-      p64 += s64 * nppi; p32 += s32 * nppi;
-      f64 += (double)a.f_pq[cp] * nppi * s64 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * n64;
-      f32 += (double)a.f_pq[cp] * nppi * s32 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * (keep - n64);
-      g64 += (double)a.f_q[cp] * n64;
-      g32 += (double)a.f_q[cp] * (keep - n64);
+      for (int k = 0; k < NBK; ++k) {
+        const int g = (Y * a.nmol + m) * NBK + k;
+        const int f = a.bseg_first[g];
+        int n = a.bseg_first[g + 1] - f;
+        // same class: kets at or before the bra in pair order (ab >= cd once)
+        if (Y == X) n = max(0, min(n, i - f + 1));
+        const int keep = count_prefix(a.Q, f, n, Qi, a.thresh);
+        int n64 = keep;
+        if (a.mixed) n64 = min(keep, count_prefix(a.Q, f, n, Qi, a.split));
+        const long long o = a.cnt_off[cp] + (long long)(i - a.cls_first[X]) * NBK + k;
+        a.cnt64[o] = n64;
+        a.cnt32[o] = keep - n64;
+        a.kst64[o] = f - a.cls_first[Y];
+        a.kst32[o] = f - a.cls_first[Y] + n64;
+        q64 += n64; q32 += keep - n64; tot += n;
+        const unsigned long long s64 = a.cumppn[f + n64] - a.cumppn[f];
+        const unsigned long long s32 = a.cumppn[f + keep] - a.cumppn[f + n64];
+        p64 += s64 * nppi; p32 += s32 * nppi;
+        f64 += (double)a.f_pq[cp] * nppi * s64 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * n64;
+        f32 += (double)a.f_pq[cp] * nppi * s32 + ((double)a.f_bra[cp] * nppi + a.f_q[cp]) * (keep - n64);
+        g64 += (double)a.f_q[cp] * n64;
+        g32 += (double)a.f_q[cp] * (keep - n64);
+      }
     }
   }
   // warp-reduce the statistics, one atomic per warp
@@ -448,7 +454,7 @@ static ClassFlops class_flops(int la, int lb, int lc, int ld) {
 struct ScanArgs {
   long long cnt_off[NCP];
   long long pre_off[NCP];
-  int nbra[NCP];
+  int nseg[NCP];            // NBK x bras of the class pair
   const int* cnt64;
   const int* cnt32;
   long long* pre64;
@@ -457,7 +463,7 @@ struct ScanArgs {
 
 __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
   const int seg = blockIdx.x >> 1, band = blockIdx.x & 1;
-  const int n = a.nbra[seg];
+  const int n = a.nseg[seg];
   const int* cnt = (band ? a.cnt32 : a.cnt64) + a.cnt_off[seg];
   long long* pre = (band ? a.pre32 : a.pre64) + a.pre_off[seg];
   __shared__ long long warp_sums[32];
@@ -684,7 +690,7 @@ static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStrea
   memcpy(sa.cls_first, b->cls_first, sizeof(sa.cls_first));
   memcpy(sa.cnt_off, b->cnt_off, sizeof(sa.cnt_off));
   sa.nmol = b->nmol;
-  sa.seg_first = b->d_seg_first;
+  sa.bseg_first = b->d_bseg_first;
   sa.pair_mol = b->nmol > 1 ? b->d_pair_mol : nullptr;
   sa.Q = b->d_pair_Q; sa.ppn = b->d_pair_ppn; sa.cumppn = b->d_cumppn;
   sa.thresh = o->thresh;
@@ -707,7 +713,7 @@ static int prepare(adft_basis* b, const double* D, const adft_opts* o, cudaStrea
       const int cp = cp_index(X, Y);
       sc.cnt_off[cp] = b->cnt_off[cp];
       sc.pre_off[cp] = b->pre_off[cp];
-      sc.nbra[cp] = b->cls_first[X + 1] - b->cls_first[X];
+      sc.nseg[cp] = NBK * (b->cls_first[X + 1] - b->cls_first[X]);
     }
   sc.cnt64 = w.cnt64; sc.cnt32 = w.cnt32; sc.pre64 = w.pre64; sc.pre32 = w.pre32;
   k_scan<<<2 * NCP, 1024, 0, s>>>(sc);
@@ -743,7 +749,7 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
         if (nX == 0 || nY == 0) continue;
         const int cp = cp_index(X, Y);
         if (o->pair_mask && !o->pair_mask[band * NCP + cp]) continue;  // another rank's share
-        L.bra_first = b->cls_first[X]; L.nbra = nX; L.ket_first = b->cls_first[Y];
+        L.bra_first = b->cls_first[X]; L.nseg = NBK * nX; L.ket_first = b->cls_first[Y];
         L.same_class = (X == Y);
         L.prefix = (band ? w.pre32 : w.pre64) + b->pre_off[cp];
         L.ket_start = (band ? w.kst32 : w.kst64) + b->cnt_off[cp];
@@ -943,7 +949,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
       (st = upload(b, &b->d_ncoefs, b->ncoefs)) || (st = upload(b, &b->d_mol_nc, b->mol_nc)) ||
       (st = upload(b, &b->d_mol_nbf, b->mol_nbf)) || (st = upload(b, &b->d_mol_cf_off, b->mol_cf_off)) ||
       (st = upload(b, &b->d_mol_f_off, b->mol_f_off)) || (st = upload(b, &b->d_mol_cbase, b->mol_cbase)) ||
-      (st = upload(b, &b->d_mol_obase, b->mol_obase)) || (st = upload(b, &b->d_seg_first, b->seg_first)))
+      (st = upload(b, &b->d_mol_obase, b->mol_obase)))
     return st;
   {
     std::vector<int> fs, fc, cs, cc;
@@ -1049,13 +1055,29 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
     }
     for (double& q : Q) q = sqrt(q);  // the kernel leaves max |(mn|mn)|
     const double qpmax = Qp.empty() ? 0.0 : *std::max_element(Qp.begin(), Qp.end());
+    // kept primitive pairs of every pair, then the order inside each (class,
+    // molecule) segment: contraction bucket of that count, then descending Q
+    std::vector<int> kept(b->npair, 0);
+    for (int o = 0; o < b->npair; ++o)
+      for (int k = ppoff[o]; k < ppoff[o] + ppn[o]; ++k) kept[o] += (Qp[k] * qpmax > PRIM_EPS);
     std::vector<int> idx(b->npair);
     std::iota(idx.begin(), idx.end(), 0);
+    b->bseg_first.assign((size_t)NCLS * b->nmol * NBK + 1, 0);
     for (int X = 0; X < NCLS; ++X)
-      for (int m = 0; m < b->nmol; ++m)
-        std::stable_sort(idx.begin() + b->seg_first[X * (b->nmol + 1) + m],
-                         idx.begin() + b->seg_first[X * (b->nmol + 1) + m + 1],
-                         [&](int i, int j) { return Q[i] > Q[j]; });
+      for (int m = 0; m < b->nmol; ++m) {
+        const int s0 = b->seg_first[X * (b->nmol + 1) + m], s1 = b->seg_first[X * (b->nmol + 1) + m + 1];
+        std::stable_sort(idx.begin() + s0, idx.begin() + s1, [&](int i, int j) {
+          const int bi = pp_bucket(kept[i]), bj = pp_bucket(kept[j]);
+          return bi != bj ? bi < bj : Q[i] > Q[j];
+        });
+        int pos = s0;
+        for (int k = 0; k < NBK; ++k) {
+          b->bseg_first[((size_t)X * b->nmol + m) * NBK + k] = pos;
+          while (pos < s1 && pp_bucket(kept[idx[pos]]) == k) ++pos;
+        }
+      }
+    b->bseg_first[(size_t)NCLS * b->nmol * NBK] = b->npair;
+    if ((st = upload(b, &b->d_bseg_first, b->bseg_first))) return st;
     std::vector<int> sa(b->npair), sb(b->npair), nsrc, nppoff(b->npair), nppn(b->npair);
     std::vector<double> nqp;  // bound of every kept primitive pair, in the new order
     b->pair_Q.resize(b->npair);
@@ -1093,9 +1115,9 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
     for (int X = 0; X < NCLS; ++X)
       for (int Y = 0; Y <= X; ++Y) {
         const int cp = cp_index(X, Y);
-        const int nX = b->cls_first[X + 1] - b->cls_first[X];
+        const long long nseg = (long long)NBK * (b->cls_first[X + 1] - b->cls_first[X]);
         b->cnt_off[cp] = co; b->pre_off[cp] = po;
-        co += nX; po += nX + 1;
+        co += nseg; po += nseg + 1;
         b->tune_blocks[0][cp] = 4;
         b->tune_blocks[1][cp] = 8;
         b->tune_variant[0][cp] = b->tune_variant[1][cp] = 0;
@@ -1109,6 +1131,7 @@ static int build_basis(adft_basis* b, const std::vector<HostMol>& mols, int sphe
         (st = dalloc(b, &w.pre64, (size_t)po)) || (st = dalloc(b, &w.pre32, (size_t)po)) ||
         (st = dalloc(b, &w.counters, 6 * NCP)) || (st = dalloc(b, &w.status, 4)) ||
         (st = dalloc(b, &w.scal, 4)) || (st = dalloc(b, &w.Emol, (size_t)b->nmol)) || (st = dalloc(b, &w.stats, 10)) ||
+        (st = dalloc(b, &w.charges, (size_t)b->natom)) ||
         (st = dalloc(b, &w.work, 4 * NCP)))
       return st;
     ADFT_CUDA(cudaMemset(w.status, 0, 4 * sizeof(int)));
@@ -1311,6 +1334,59 @@ int adft_jk_last_stats(adft_basis* b, adft_stats* out) {
   return ADFT_OK;
 }
 
+int adft_one_electron(adft_basis* b, const double* charges, void* stream, double* S, double* T, double* V) {
+  if (!b || !charges || !S || !T || !V) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  if (b->nmol != 1) { set_error("one-electron integrals are computed for single-molecule bases"); return ADFT_ERR_ARG; }
+  for (int i = 0; i < b->natom; ++i)
+    if (!isfinite(charges[i])) { set_error("charges must be finite"); return ADFT_ERR_ARG; }
+  int st = set_device(b);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = b->ws;
+  ADFT_CUDA(cudaMemcpyAsync(w.charges, charges, sizeof(double) * b->natom, cudaMemcpyHostToDevice, s));
+  BasisView v = view(b);
+  ADFT_CUDA(launch_one_electron(v, b->d_shell_nprim, b->d_shell_poff, b->d_exps, b->d_ncoefs, w.charges, w.Jc, w.Kc,
+                                w.Dc, s));
+  if ((st = output_jk(b, s, S, T))) return st;
+  const long long nb2 = b->mol_obase[b->nmol];
+  k_from_cart<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(xform_args(b), nb2, w.Dc, w.Dc, V, w.Kw);
+  ADFT_CUDA(cudaGetLastError());
+  b->last_stream = s;
+  return ADFT_OK;
+}
+
+int adft_jk_last_class_stats(adft_basis* b, int64_t* quartets, int64_t* prim_quartets, int64_t* bra_prims,
+                             double* flops) {
+  if (!b) { set_error("NULL basis"); return ADFT_ERR_ARG; }
+  ADFT_CUDA(cudaStreamSynchronize(b->last_stream));
+  std::vector<unsigned long long> wk(4 * NCP, 0);
+  if (b->work_valid)
+    ADFT_CUDA(cudaMemcpy(wk.data(), b->ws.work, wk.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  for (int band = 0; band < 2; ++band)
+    for (int X = 0; X < NCLS; ++X)
+      for (int Y = 0; Y <= X; ++Y) {
+        const int cp = cp_index(X, Y), o = band * NCP + cp;
+        const long long nseg = (long long)NBK * (b->cls_first[X + 1] - b->cls_first[X]);
+        long long q = 0;
+        if (quartets && nseg > 0)
+          ADFT_CUDA(cudaMemcpy(&q, (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp] + nseg, sizeof(q),
+                               cudaMemcpyDeviceToHost));
+        const unsigned long long* c = wk.data() + 2 * o;
+        const ClassFlops f = class_flops(cls_la(X), cls_lb(X), cls_la(Y), cls_lb(Y));
+        if (quartets) quartets[o] = q;
+        if (prim_quartets) prim_quartets[o] = (int64_t)c[0];
+        if (bra_prims) bra_prims[o] = (int64_t)c[1];
+        if (flops) {
+          long long qq = q;
+          if (!quartets && nseg > 0)
+            ADFT_CUDA(cudaMemcpy(&qq, (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp] + nseg, sizeof(qq),
+                                 cudaMemcpyDeviceToHost));
+          flops[o] = f.per_pq * (double)c[0] + f.per_bra * (double)c[1] + f.per_q * (double)qq;
+        }
+      }
+  return ADFT_OK;
+}
+
 int adft_jk_last_timings(adft_basis* b, double* ms) {
   if (!b || !ms) { set_error("NULL argument"); return ADFT_ERR_ARG; }
   if (!b->ev_valid) { set_error("no completed call to time"); return ADFT_ERR_ARG; }
@@ -1372,7 +1448,7 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table
         const int cp = cp_index(X, Y);
         if (b->cls_first[X + 1] == b->cls_first[X] || b->cls_first[Y + 1] == b->cls_first[Y]) continue;
         JKLaunch L = base_launch(b);
-        L.bra_first = b->cls_first[X]; L.nbra = b->cls_first[X + 1] - b->cls_first[X];
+        L.bra_first = b->cls_first[X]; L.nseg = NBK * (b->cls_first[X + 1] - b->cls_first[X]);
         L.ket_first = b->cls_first[Y]; L.same_class = (X == Y);
         L.prefix = (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp];
         L.ket_start = (band ? b->ws.kst32 : b->ws.kst64) + b->cnt_off[cp];
@@ -1421,7 +1497,7 @@ int adft_jk_plan(adft_basis* b, const double* D, const adft_opts* o, adft_stats*
           const int cp = cp_index(X, Y);
           const int nX = b->cls_first[X + 1] - b->cls_first[X];
           long long v = 0;
-          ADFT_CUDA(cudaMemcpy(&v, (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp] + nX, sizeof(v),
+          ADFT_CUDA(cudaMemcpy(&v, (band ? b->ws.pre32 : b->ws.pre64) + b->pre_off[cp] + (long long)NBK * nX, sizeof(v),
                                cudaMemcpyDeviceToHost));
           quartets[band * NCP + cp] = v;
         }

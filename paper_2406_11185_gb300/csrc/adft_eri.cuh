@@ -61,13 +61,6 @@ template <typename T> __device__ __forceinline__ T from_f64(double x) { return (
 template <typename T> constexpr bool is_f64 = std::is_same<T, double>::value;
 template <typename T> constexpr bool is_f32 = std::is_same<T, float>::value;
 
-// chunk of ket components owned by one thread
-template <int NAB, int NHAB, int NCD, int BUDGET>
-struct ChunkPlan {
-  static constexpr int raw = BUDGET / (NAB + NHAB);
-  static constexpr int CK = raw < 1 ? 1 : (raw > NCD ? NCD : raw);
-  static constexpr int NCHUNK = (NCD + CK - 1) / CK;
-};
 
 template <typename T> struct Prec;
 template <> struct Prec<double> {
@@ -215,42 +208,36 @@ __device__ __forceinline__ void hermite_E(T PA, T PB, T o2p, T* E) {
 }
 
 // Hermite Coulomb integrals R_tuv, t+u+v <= L (Helgaker eqs. 9.9.18-9.9.20),
-// from the base values B_n = R^n_000, raised in t, u or v from layer n+1.
+// from the base values B_n = R^n_000, raised in t, u or v from layer n+1, in
+// place: layer n overwrites layer n+1, and inside a layer the entries are
+// produced by decreasing t+u+v, so an entry is overwritten only after every
+// entry of the new layer that reads it has been computed.
 template <typename T, int L>
 __device__ __forceinline__ void hermite_R(const T* B, T X, T Y, T Z, T* R) {
-  T tmp[nherm(L)];
 #pragma unroll
-  for (int n = L; n >= 0; --n) {
-    // layer n goes to R when (L - n) is even, else to tmp; layer n+1 is in the other
-    T* dst = ((L - n) % 2 == 0) ? R : tmp;
-    const T* src = ((L - n) % 2 == 0) ? tmp : R;
+  for (int n = L; n >= 0; --n)
 #pragma unroll
-    for (int t = 0; t <= L - n; ++t)
+    for (int s = L - n; s >= 0; --s)
 #pragma unroll
-      for (int u = 0; u <= L - n - t; ++u)
+      for (int t = s; t >= 0; --t)
 #pragma unroll
-        for (int v = 0; v <= L - n - t - u; ++v) {
+        for (int u = s - t; u >= 0; --u) {
+          const int v = s - t - u;
           T val;
-          if (t == 0 && u == 0 && v == 0) {
+          if (s == 0) {
             val = B[n];
           } else if (t > 0) {
-            val = X * src[hidx(t - 1, u, v)];
-            if (t > 1) val += T(t - 1) * src[hidx(t - 2, u, v)];
+            val = X * R[hidx(t - 1, u, v)];
+            if (t > 1) val += T(t - 1) * R[hidx(t - 2, u, v)];
           } else if (u > 0) {
-            val = Y * src[hidx(t, u - 1, v)];
-            if (u > 1) val += T(u - 1) * src[hidx(t, u - 2, v)];
+            val = Y * R[hidx(t, u - 1, v)];
+            if (u > 1) val += T(u - 1) * R[hidx(t, u - 2, v)];
           } else {
-            val = Z * src[hidx(t, u, v - 1)];
-            if (v > 1) val += T(v - 1) * src[hidx(t, u, v - 2)];
+            val = Z * R[hidx(t, u, v - 1)];
+            if (v > 1) val += T(v - 1) * R[hidx(t, u, v - 2)];
           }
-          dst[hidx(t, u, v)] = val;
+          R[hidx(t, u, v)] = val;
         }
-  }
-  if constexpr (L % 2 == 1) {
-    // layer 0 landed in tmp
-#pragma unroll
-    for (int x = 0; x < nherm(L); ++x) R[x] = tmp[x];
-  }
 }
 
 // Base values R^n_000 and the Hermite integrals of one primitive quartet.
@@ -286,15 +273,28 @@ __device__ __forceinline__ void prim_R(T alpha, T X, T Y, T Z, const BasisView& 
 }
 
 // ---------------------------------------------------------------------------
-// Contracted Cartesian block of one shell quartet for the ket components
-// [chunk*CK, chunk*CK + CK): G[ab*CK + k] = (a b | c d)_k.
-// Primitive quartets with Q_p Q_q < eps are skipped; npq and nbp are
-// increased by the primitive quartets and bra primitives evaluated.
-template <typename T, int LA, int LB, int LC, int LD, int CK>
-__device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int ket, int chunk, T* G, T eps,
-                                              int& npq, int& nbp) {
-  constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
-  constexpr int NAB = NA * NB, NCD = NC * ND;
+// Compile-time loop: f(std::integral_constant<int, i>{}) for i = 0 .. N-1.
+// Component indices handed out this way are constants, so every loop bound
+// and array index derived from them folds at compile time and the thread's
+// arrays stay in registers.
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_seq(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_seq(f, std::make_integer_sequence<int, N>{});
+}
+
+// Contracted Cartesian block of one shell quartet, G[ab*NCD + cd] = (ab|cd),
+// all components in one thread (small classes).  Primitive quartets with
+// Q_p Q_q < eps are skipped; npq and nbp are increased by the primitive
+// quartets and bra primitives evaluated.
+template <typename T, int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int ket, T* G, T eps, int& npq,
+                                              int& nbp) {
+  constexpr int NB = ncart(LB), ND = ncart(LD);
+  constexpr int NAB = ncart(LA) * NB, NCD = ncart(LC) * ND;
   constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
   constexpr int NHAB = nherm(LAB);
   constexpr int EA = (LA + 1) * (LB + 1) * (LAB + 1), EC = (LC + 1) * (LD + 1) * (LCD + 1);
@@ -308,19 +308,8 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
   const T CDx = from_f64<T>(__ldg(bv.pair_AB + 3 * ket)), CDy = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 1)),
           CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
 
-  // powers of the owned ket components
-  int cp[CK][6];
 #pragma unroll
-  for (int k = 0; k < CK; ++k) {
-    int kc = chunk * CK + k;
-    if (kc >= NCD) kc = NCD - 1;  // padded slot, never digested
-    const int ic = kc / ND, id = kc % ND;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) { cp[k][d] = cart_pow(LC, ic, d); cp[k][3 + d] = cart_pow(LD, id, d); }
-  }
-
-#pragma unroll
-  for (int x = 0; x < NAB * CK; ++x) G[x] = T(0);
+  for (int x = 0; x < NAB * NCD; ++x) G[x] = T(0);
 
   const float* __restrict__ qa = bv.pp_q32;
   const float epsf = (float)eps;
@@ -337,9 +326,9 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
     hermite_E<T, LA, LB>(bp.PAy, bp.PAy + ABy, o2p, Eab[1]);
     hermite_E<T, LA, LB>(bp.PAz, bp.PAz + ABz, o2p, Eab[2]);
 
-    T W[NHAB * CK];
+    T W[NHAB * NCD];
 #pragma unroll
-    for (int x = 0; x < NHAB * CK; ++x) W[x] = T(0);
+    for (int x = 0; x < NHAB * NCD; ++x) W[x] = T(0);
 
     for (int iq = 0; iq < n1e; ++iq) {
       const PrimPair<T> kq = pp[off1 + iq];
@@ -354,15 +343,20 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
       T R[nherm(L)];
       prim_R<T, L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
       const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+      // ket transform W[tuv][cd] += sum_{tau nu phi} (+-) E^cd R_{t+tau, u+nu, v+phi}
+      static_for<NCD>([&](auto kk) {
+        constexpr int kc = decltype(kk)::value;
+        constexpr int cx = cart_x(LC, kc / ND), cy = cart_y(LC, kc / ND), cz = cart_z(LC, kc / ND);
+        constexpr int dx = cart_x(LD, kc % ND), dy = cart_y(LD, kc % ND), dz = cart_z(LD, kc % ND);
 #pragma unroll
-      for (int k = 0; k < CK; ++k) {
-        const int cx = cp[k][0], cy = cp[k][1], cz = cp[k][2], dx = cp[k][3], dy = cp[k][4], dz = cp[k][5];
         for (int tau = 0; tau <= cx + dx; ++tau) {
-          const T ex = Ecd[0][(cx * (LD + 1) + dx) * NTC + tau];
+          const T ex = pref * Ecd[0][(cx * (LD + 1) + dx) * NTC + tau];
+#pragma unroll
           for (int nu = 0; nu <= cy + dy; ++nu) {
             const T exy = ex * Ecd[1][(cy * (LD + 1) + dy) * NTC + nu];
+#pragma unroll
             for (int phi = 0; phi <= cz + dz; ++phi) {
-              T e2 = pref * exy * Ecd[2][(cz * (LD + 1) + dz) * NTC + phi];
+              T e2 = exy * Ecd[2][(cz * (LD + 1) + dz) * NTC + phi];
               if ((tau + nu + phi) & 1) e2 = -e2;
               // all bra Hermite functions (t,u,v), t+u+v <= LAB
 #pragma unroll
@@ -372,31 +366,31 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
 #pragma unroll
                   for (int v = 0; v <= m; ++v) {
                     const int t = n - m, u = m - v;
-                    W[hidx(t, u, v) * CK + k] += e2 * R[hidx(t + tau, u + nu, v + phi)];
+                    W[hidx(t, u, v) * NCD + kc] += e2 * R[hidx(t + tau, u + nu, v + phi)];
                   }
             }
           }
         }
-      }
+      });
     }
     // bra transform of this bra primitive
-#pragma unroll
-    for (int ab = 0; ab < NAB; ++ab) {
-      const int ia = ab / NB, ib = ab % NB;
-      const int ax = cart_pow(LA, ia, 0), ay = cart_pow(LA, ia, 1), az = cart_pow(LA, ia, 2);
-      const int bx = cart_pow(LB, ib, 0), by = cart_pow(LB, ib, 1), bz = cart_pow(LB, ib, 2);
+    static_for<NAB>([&](auto abk) {
+      constexpr int ab = decltype(abk)::value;
+      constexpr int ax = cart_x(LA, ab / NB), ay = cart_y(LA, ab / NB), az = cart_z(LA, ab / NB);
+      constexpr int bx = cart_x(LB, ab % NB), by = cart_y(LB, ab % NB), bz = cart_z(LB, ab % NB);
 #pragma unroll
       for (int t = 0; t <= ax + bx; ++t)
 #pragma unroll
-        for (int u = 0; u <= ay + by; ++u)
+        for (int u = 0; u <= ay + by; ++u) {
+          const T exy = bp.K * Eab[0][(ax * (LB + 1) + bx) * NTA + t] * Eab[1][(ay * (LB + 1) + by) * NTA + u];
 #pragma unroll
           for (int v = 0; v <= az + bz; ++v) {
-            const T e1 = bp.K * Eab[0][(ax * (LB + 1) + bx) * NTA + t] * Eab[1][(ay * (LB + 1) + by) * NTA + u] *
-                         Eab[2][(az * (LB + 1) + bz) * NTA + v];
+            const T e1 = exy * Eab[2][(az * (LB + 1) + bz) * NTA + v];
 #pragma unroll
-            for (int k = 0; k < CK; ++k) G[ab * CK + k] += e1 * W[hidx(t, u, v) * CK + k];
+            for (int kc = 0; kc < NCD; ++kc) G[ab * NCD + kc] += e1 * W[hidx(t, u, v) * NCD + kc];
           }
-    }
+        }
+    });
   }
 }
 
@@ -755,104 +749,198 @@ __device__ __noinline__ void digest_rt(const RtClass& C, const JKLaunch& a, int 
 
 // ---------------------------------------------------------------------------
 // work decoding: quartet index -> (bra, ket) by binary search over the
-// per-bra prefix of kept kets (the implicit class-sorted work list).
+// prefix of kept kets per (bra, bucket) segment (the implicit class-sorted
+// work list).  The segment found is the last one starting at or before qi,
+// which is never an empty one.
 __device__ __forceinline__ void decode_quartet(const JKLaunch& a, long long qi, int& bra, int& ket) {
-  int lo = 0, hi = a.nbra;
+  int lo = 0, hi = a.nseg;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (__ldg(a.prefix + mid) <= qi) lo = mid; else hi = mid;
   }
   const long long j = qi - __ldg(a.prefix + lo) + __ldg(a.ket_start + lo);
-  bra = a.bra_first + lo;
+  bra = a.bra_first + lo / NBK;
+  ket = a.ket_first + (int)j;
+}
+
+// The same for the items base + d of a warp (0 <= d < 32, every lane of the
+// warp calls it): a 32-ary search by the whole warp for the segment of base,
+// then each lane finds its own segment among the next 32 segment starts by a
+// binary search over the lanes' registers (segments beyond those 32, e.g.
+// after a run of empty ones, fall back to decode_quartet).
+__device__ __forceinline__ void decode_warp(const JKLaunch& a, long long base, int d, int& bra, int& ket) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = a.nseg;  // prefix[lo] <= base < prefix[hi]
+  while (hi - lo > 32) {
+    const long long span = hi - lo;
+    const int p = lo + (int)((span * lane) >> 5);
+    const unsigned le = __ballot_sync(0xffffffffu, __ldg(a.prefix + p) <= base);
+    const int k = 31 - __clz(le);  // lane 0 probes lo, so k >= 0
+    const int nlo = lo + (int)((span * k) >> 5);
+    hi = k == 31 ? hi : lo + (int)((span * (k + 1)) >> 5);
+    lo = nlo;
+  }
+  // r_j: start of segment lo + 1 + j relative to base (33 = beyond the list)
+  const int idx = lo + 1 + lane;
+  const long long pj = idx <= a.nseg ? __ldg(a.prefix + idx) : base + 33;
+  const int rj = (int)min(max(pj - base, 0LL), 33LL);
+  int c = 0;  // number of j with r_j <= d (r is non-decreasing in j)
+#pragma unroll
+  for (int st = 16; st > 0; st >>= 1) {
+    const int r = __shfl_sync(0xffffffffu, rj, c + st - 1);
+    if (r <= d) c += st;
+  }
+  if (__shfl_sync(0xffffffffu, rj, c & 31) <= d && c < 32) ++c;
+  const long long pstart = __shfl_sync(0xffffffffu, pj, (c + 31) & 31);
+  if (c == 32) {  // past the 32 segment starts held by the warp
+    decode_quartet(a, base + d, bra, ket);
+    return;
+  }
+  const int seg = lo + c;
+  const long long start = c == 0 ? __ldg(a.prefix + lo) : pstart;
+  const long long j = base + d - start + __ldg(a.ket_start + seg);
+  bra = a.bra_first + seg / NBK;
   ket = a.ket_first + (int)j;
 }
 
 // J/K digestion of one quartet block (Cartesian, unsymmetrised accumulators):
 // with w = s_ab s_cd s_(ab,cd) (1/2 for each coincidence)
-//   J_mn += 4w sum_ls g D_ls,   J_ls += 4w sum_mn g D_mn,
-//   K_ml += 2w sum_ns g D_ns,   K_nl += 2w sum_ms g D_ms,
-//   K_ms += 2w sum_nl g D_nl,   K_ns += 2w sum_ml g D_ml,
+//   J_ab += 4w sum_cd g D_cd,        J_cd += 4w sum_ab g D_ab,
+//   K_ac += 2w sum_bd g D_bd,        K_ad += 2w sum_bc g D_bc,
+//   K_bc += 2w sum_ad g D_ad,        K_bd += 2w sum_ac g D_ac,
 // which after X <- (X + X^T)/2 equals the sum over all 8 index permutations.
-template <typename T, int LA, int LB, int LC, int LD, int CK>
-__device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, int chunk, const T* G) {
+// Each thread reads every D element it needs once and sums over both inner
+// indices before its atomic, so a quartet issues NAB + NCD + (NA+NB)(NC+ND)
+// FP64 atomics.  All 32 lanes call it (valid = 0 for a lane without a
+// quartet); when every valid lane of the warp holds the same bra pair, the
+// J_ab sums are reduced across the warp first and one lane adds them.
+template <typename T, int LA, int LB, int LC, int LD>
+__device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, bool valid, const T* G) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
-  constexpr int NCD = NC * ND;
+  constexpr int NAB = NA * NB, NCD = NC * ND;
   const BasisView& bv = a.bv;
-  const int sa = __ldg(bv.pair_a + bra), sb = __ldg(bv.pair_b + bra);
-  const int sc = __ldg(bv.pair_a + ket), sd = __ldg(bv.pair_b + ket);
-  const int oa = __ldg(bv.shell_coff + sa), ob = __ldg(bv.shell_coff + sb);
-  const int oc = __ldg(bv.shell_coff + sc), od = __ldg(bv.shell_coff + sd);
-  long long base;
-  long n;
-  mol_block(bv, bra, base, n);
-  T w = T(1);
-  if (sa == sb) w *= cst<T>(0.5);
-  if (sc == sd) w *= cst<T>(0.5);
-  if (a.same_class && bra == ket) w *= cst<T>(0.5);
-  const T w4 = T(4) * w, w2 = T(2) * w;
-  const T* __restrict__ D = nullptr;
-  D = dmat<T>(a) + base;
-  double* __restrict__ Jm = a.J + base;
-  double* __restrict__ Km = a.K + base;
-
-  // J_ab += 4w sum_cd g D_cd
-  T Dcd[CK];
+  const int lane = threadIdx.x & 31;
+  const int bra0 = __shfl_sync(0xffffffffu, valid ? bra : -1, __ffs(__ballot_sync(0xffffffffu, valid)) - 1);
+  const bool warp_bra = __all_sync(0xffffffffu, !valid || bra == bra0);
+  T jab[NAB];
+  int oa = 0, ob = 0;
+  long long base = 0;
+  long n = 0;
+  T w4 = T(0);
+  if (valid) {
+    const int sa = __ldg(bv.pair_a + bra), sb = __ldg(bv.pair_b + bra);
+    const int sc = __ldg(bv.pair_a + ket), sd = __ldg(bv.pair_b + ket);
+    oa = __ldg(bv.shell_coff + sa); ob = __ldg(bv.shell_coff + sb);
+    const int oc = __ldg(bv.shell_coff + sc), od = __ldg(bv.shell_coff + sd);
+    mol_block(bv, bra, base, n);
+    T w = T(1);
+    if (sa == sb) w *= cst<T>(0.5);
+    if (sc == sd) w *= cst<T>(0.5);
+    if (a.same_class && bra == ket) w *= cst<T>(0.5);
+    w4 = T(4) * w;
+    const T w2 = T(2) * w;
+    const T* __restrict__ D = dmat<T>(a) + base;
+    double* __restrict__ Jm = a.J + base;
+    double* __restrict__ Km = a.K + base;
+    T Dcd[NCD], Dab[NAB], Dbd[NB * ND], Dbc[NB * NC], Dad[NA * ND], Dac[NA * NC];
 #pragma unroll
-  for (int k = 0; k < CK; ++k) {
-    const int kc = chunk * CK + k;
-    Dcd[k] = (kc < NCD) ? dload(D + (oc + kc / ND) * n + od + kc % ND) : T(0);
-  }
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-  for (int ia = 0; ia < NA; ++ia)
+      for (int d = 0; d < ND; ++d) Dcd[c * ND + d] = dload(D + (oc + c) * n + od + d);
 #pragma unroll
-    for (int ib = 0; ib < NB; ++ib) {
+    for (int x = 0; x < NA; ++x)
+#pragma unroll
+      for (int y = 0; y < NB; ++y) Dab[x * NB + y] = dload(D + (oa + x) * n + ob + y);
+#pragma unroll
+    for (int y = 0; y < NB; ++y) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d) Dbd[y * ND + d] = dload(D + (ob + y) * n + od + d);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) Dbc[y * NC + c] = dload(D + (ob + y) * n + oc + c);
+    }
+#pragma unroll
+    for (int x = 0; x < NA; ++x) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d) Dad[x * ND + d] = dload(D + (oa + x) * n + od + d);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) Dac[x * NC + c] = dload(D + (oa + x) * n + oc + c);
+    }
+    // J_ab (added below, possibly after a warp reduction)
+#pragma unroll
+    for (int ab = 0; ab < NAB; ++ab) {
       T s = T(0);
 #pragma unroll
-      for (int k = 0; k < CK; ++k) s += G[(ia * NB + ib) * CK + k] * Dcd[k];
-      atomicAdd(Jm + (oa + ia) * n + ob + ib, (double)(w4 * s));
+      for (int cd = 0; cd < NCD; ++cd) s += G[ab * NCD + cd] * Dcd[cd];
+      jab[ab] = s;
     }
-  // J_cd += 4w sum_ab g D_ab
+    // J_cd
 #pragma unroll
-  for (int k = 0; k < CK; ++k) {
-    const int kc = chunk * CK + k;
-    if (kc >= NCD) break;
-    T s = T(0);
+    for (int cd = 0; cd < NCD; ++cd) {
+      T s = T(0);
 #pragma unroll
-    for (int ia = 0; ia < NA; ++ia)
+      for (int ab = 0; ab < NAB; ++ab) s += G[ab * NCD + cd] * Dab[ab];
+      atomicAdd(Jm + (oc + cd / ND) * n + od + cd % ND, (double)(w4 * s));
+    }
+    // K_ac, K_ad
 #pragma unroll
-      for (int ib = 0; ib < NB; ++ib) s += G[(ia * NB + ib) * CK + k] * dload(D + (oa + ia) * n + ob + ib);
-    atomicAdd(Jm + (oc + kc / ND) * n + od + kc % ND, (double)(w4 * s));
+    for (int x = 0; x < NA; ++x) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T s = T(0);
+#pragma unroll
+        for (int y = 0; y < NB; ++y)
+#pragma unroll
+          for (int d = 0; d < ND; ++d) s += G[(x * NB + y) * NCD + c * ND + d] * Dbd[y * ND + d];
+        atomicAdd(Km + (oa + x) * n + oc + c, (double)(w2 * s));
+      }
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        T s = T(0);
+#pragma unroll
+        for (int y = 0; y < NB; ++y)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s += G[(x * NB + y) * NCD + c * ND + d] * Dbc[y * NC + c];
+        atomicAdd(Km + (oa + x) * n + od + d, (double)(w2 * s));
+      }
+    }
+    // K_bc, K_bd
+#pragma unroll
+    for (int y = 0; y < NB; ++y) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T s = T(0);
+#pragma unroll
+        for (int x = 0; x < NA; ++x)
+#pragma unroll
+          for (int d = 0; d < ND; ++d) s += G[(x * NB + y) * NCD + c * ND + d] * Dad[x * ND + d];
+        atomicAdd(Km + (ob + y) * n + oc + c, (double)(w2 * s));
+      }
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        T s = T(0);
+#pragma unroll
+        for (int x = 0; x < NA; ++x)
+#pragma unroll
+          for (int c = 0; c < NC; ++c) s += G[(x * NB + y) * NCD + c * ND + d] * Dac[x * NC + c];
+        atomicAdd(Km + (ob + y) * n + od + d, (double)(w2 * s));
+      }
+    }
   }
-  // K contributions
+  // J_ab: one atomic per element per warp when the whole warp shares the bra
+  // (the work list is bra-major, so this is the common case)
+  if (warp_bra) {
 #pragma unroll
-  for (int k = 0; k < CK; ++k) {
-    const int kc = chunk * CK + k;
-    if (kc >= NCD) break;
-    const int ic = kc / ND, id = kc % ND;
+    for (int ab = 0; ab < NAB; ++ab) {
+      double v = valid ? (double)(w4 * jab[ab]) : 0.0;
 #pragma unroll
-    for (int ia = 0; ia < NA; ++ia) {
-      T s_ac = T(0), s_ad = T(0);
-#pragma unroll
-      for (int ib = 0; ib < NB; ++ib) {
-        const T g = G[(ia * NB + ib) * CK + k];
-        s_ac += g * dload(D + (ob + ib) * n + od + id);
-        s_ad += g * dload(D + (ob + ib) * n + oc + ic);
-      }
-      atomicAdd(Km + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
-      atomicAdd(Km + (oa + ia) * n + od + id, (double)(w2 * s_ad));
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      jab[ab] = (T)0;
+      if (lane == __ffs(__ballot_sync(0xffffffffu, valid)) - 1)
+        atomicAdd(a.J + base + (oa + ab / NB) * n + ob + ab % NB, v);
     }
+  } else if (valid) {
 #pragma unroll
-    for (int ib = 0; ib < NB; ++ib) {
-      T s_bc = T(0), s_bd = T(0);
-#pragma unroll
-      for (int ia = 0; ia < NA; ++ia) {
-        const T g = G[(ia * NB + ib) * CK + k];
-        s_bc += g * dload(D + (oa + ia) * n + od + id);
-        s_bd += g * dload(D + (oa + ia) * n + oc + ic);
-      }
-      atomicAdd(Km + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
-      atomicAdd(Km + (ob + ib) * n + od + id, (double)(w2 * s_bd));
-    }
+    for (int ab = 0; ab < NAB; ++ab) atomicAdd(a.J + base + (oa + ab / NB) * n + ob + ab % NB, (double)(w4 * jab[ab]));
   }
 }
 
@@ -869,12 +957,11 @@ __host__ __device__ constexpr bool is_small_class(int la, int lb, int lc, int ld
   return la + lb + lc + ld <= 4 && ncart(la) * ncart(lb) * ncart(lc) * ncart(ld) <= 81;
 }
 
+// Small classes: one thread per quartet with the whole block in registers.
 template <typename T, int LA, int LB, int LC, int LD>
 __global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
   constexpr int NAB = ncart(LA) * ncart(LB), NCD = ncart(LC) * ncart(LD);
-  using Plan = ChunkPlan<NAB, nherm(LA + LB), NCD, Prec<T>::BUDGET>;
-  constexpr int CK = Plan::CK, NCHUNK = Plan::NCHUNK;
-  const long long total = (long long)__ldg(a.prefix + a.nbra) * NCHUNK;
+  const long long total = (long long)__ldg(a.prefix + a.nseg);
   const int lane = threadIdx.x & 31;
   unsigned cpq = 0, cbp = 0;
   for (;;) {
@@ -887,17 +974,17 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
       break;
     }
     const long long item = (long long)base + lane;
-    if (item < total) {
-      const long long qi = item / NCHUNK;
-      const int chunk = (int)(item - qi * NCHUNK);
-      int bra, ket;
-      decode_quartet(a, qi, bra, ket);
-      T G[NAB * CK];
+    const bool valid = item < total;
+    int bra = 0, ket = 0;
+    T G[NAB * NCD];
+    decode_warp(a, (long long)base, valid ? lane : 0, bra, ket);
+    if (valid) {
       int npq = 0, nbp = 0;
-      quartet_block<T, LA, LB, LC, LD, CK>(a.bv, bra, ket, chunk, G, (T)a.prim_eps, npq, nbp);
-      if (chunk == 0) { cpq += npq; cbp += nbp; }  // count each quartet once
-      digest<T, LA, LB, LC, LD, CK>(a, bra, ket, chunk, G);
+      quartet_block<T, LA, LB, LC, LD>(a.bv, bra, ket, G, (T)a.prim_eps, npq, nbp);
+      cpq += npq;
+      cbp += nbp;
     }
+    digest<T, LA, LB, LC, LD>(a, bra, ket, valid, G);
   }
   flush_work(a.work, cpq, cbp);
 }
@@ -909,7 +996,7 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
   constexpr int EA = (LA + 1) * (LB + 1) * (LAB + 1), EC = (LC + 1) * (LD + 1) * (LCD + 1);
   using S = RtSizes<(EA > EC ? EA : EC), nherm(LAB + LCD), nherm(LAB) * C.ck>;
   constexpr int NG = ncart(LA) * ncart(LB) * C.ck;
-  const long long total = (long long)__ldg(a.prefix + a.nbra) * C.nchunk;
+  const long long total = (long long)__ldg(a.prefix + a.nseg) * C.nchunk;
   const int lane = threadIdx.x & 31;
   T G[NG];
   unsigned cpq = 0, cbp = 0;

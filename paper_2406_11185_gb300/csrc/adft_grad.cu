@@ -83,7 +83,7 @@ __device__ __noinline__ void centre_derivative(const BasisView& bv, int P, int Q
 template <typename T>
 __global__ void __launch_bounds__(JK_THREADS) k_grad_generic(GradLaunch g, int la, int lb, int lc, int ld) {
   const JKLaunch& a = g.jk;
-  const long long total = (long long)__ldg(a.prefix + a.nbra);
+  const long long total = (long long)__ldg(a.prefix + a.nseg);
   const int lane = threadIdx.x & 31;
   T Gp[GEN_BUDGET], Gm[GEN_BUDGET];
   const T* D = nullptr;

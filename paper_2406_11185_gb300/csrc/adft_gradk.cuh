@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_grad_coop(GradLaunch gl
   T* Gam = gbase + P::REGION;                                         // [NAB][NCD]
   T* Eab = Gam + NAB * NCD;                                           // [3][EA1] raised bra E
   const unsigned gmask = (GS == 32) ? 0xffffffffu : (((1u << GS) - 1u) << (g * GS));
-  const long long total = (long long)__ldg(a.prefix + a.nbra);
+  const long long total = (long long)__ldg(a.prefix + a.nseg);
   const BasisView& bv = a.bv;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
   const T* __restrict__ o2pa = Prec<T>::o2p(bv);

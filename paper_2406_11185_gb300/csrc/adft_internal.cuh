@@ -81,14 +81,27 @@ __device__ __forceinline__ void mol_block(const BasisView& bv, int pair, long lo
   }
 }
 
-// One class-pair launch of the J/K kernel.
+// Contraction buckets.  Inside each (class, molecule) segment the pairs are
+// ordered by bucket of their primitive-pair count, then by descending Schwarz
+// bound, so the kets a bra keeps are a Q-prefix of every bucket, and a warp's
+// consecutive quartets (same bra, neighbouring kets of one bucket) run
+// primitive loops of similar length.  Upper bounds of the buckets:
+constexpr int NBK = 10;
+__host__ __device__ constexpr int pp_bucket(int npp) {
+  return npp <= 1 ? 0 : npp <= 2 ? 1 : npp <= 4 ? 2 : npp <= 6 ? 3 : npp <= 9 ? 4 : npp <= 13 ? 5
+       : npp <= 18 ? 6 : npp <= 25 ? 7 : npp <= 36 ? 8 : 9;
+}
+
+// One class-pair launch of the J/K kernel.  The work list is implicit: one
+// segment per (bra, ket bucket), bra-major; segment s holds the kept kets of
+// bra bra_first + s / NBK in bucket s % NBK.
 struct JKLaunch {
   BasisView bv;
-  int bra_first, nbra;      // pairs of class X: [bra_first, bra_first + nbra)
+  int bra_first, nseg;      // bras of class X start at bra_first; nseg = NBK x bras
   int ket_first;            // pairs of class Y start here
   int same_class;           // X == Y
-  const long long* prefix;  // [nbra + 1] quartets before each bra
-  const int* ket_start;     // [nbra] first ket of the band, relative to ket_first
+  const long long* prefix;  // [nseg + 1] quartets before each segment
+  const int* ket_start;     // [nseg] first ket of the segment (band), relative to ket_first
   unsigned long long* counter;  // dynamic work counter (zeroed)
   const double* D64;        // Cartesian D [ncart][ncart]
   const float* D32;
@@ -131,6 +144,11 @@ cudaError_t launch_schwarz(int X, const BasisView& bv, int first, int n, int max
                            cudaStream_t s);
 cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, const int* pp_pair, int npp_class,
                                 double* Qp, cudaStream_t s);
+// Cartesian one-electron matrices S, T, V (full [ncart][ncart]) of a
+// single-molecule basis; charges: device [natom].
+cudaError_t launch_one_electron(const BasisView& bv, const int* shell_nprim, const int* shell_poff,
+                                const double* exps, const double* ncoefs, const double* charges, double* S,
+                                double* T, double* V, cudaStream_t s);
 // Primitive pairs whose bound Qp * max(Qp) is at or below this are dropped at
 // basis creation (1e-3 of the paper's default tolerance 1e-12).
 constexpr double PRIM_EPS = 1e-15;

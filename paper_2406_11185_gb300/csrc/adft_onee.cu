@@ -1,0 +1,119 @@
+// One-electron integrals of the core Hamiltonian (overlap S, kinetic energy T,
+// nuclear attraction V) for the SCF driver around the J/K build: the Fock
+// matrix of Eq. 1 (Sec. 1.2.1) is F = H + J - 1/2 c_x K with H = T + V.
+// McMurchie-Davidson (Helgaker, Jorgensen and Olsen, Sec. 9.3 and 9.9):
+//   S_ij = E^{ij}_0 sqrt(pi/p) per direction,
+//   T_ij = -1/2 [ j(j-1) S_{i,j-2} - 2b(2j+1) S_ij + 4b^2 S_{i,j+2} ] per direction
+//          (the second derivative of the ket Gaussian), T = Tx Sy Sz + ...,
+//   V = -sum_C Z_C (2 pi / p) sum_tuv E^{ij}_t E^{kl}_u E^{mn}_v R_tuv(p, P - C).
+// One thread per ordered shell pair; the blocks are written to full Cartesian
+// matrices and transformed to the output basis like J and K.  Called once per
+// geometry, so it favours simplicity over speed.
+#include "adft_eri.cuh"
+
+namespace adft {
+
+struct OneElecArgs {
+  BasisView bv;
+  const int* shell_nprim;
+  const int* shell_poff;
+  const double* exps;
+  const double* ncoefs;  // c_i N(a_i, l)
+  const double* charges; // [natom]
+  double* S;             // Cartesian [ncart][ncart]
+  double* T;
+  double* V;
+};
+
+__global__ void __launch_bounds__(128) k_one_electron(OneElecArgs g) {
+  const BasisView& bv = g.bv;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)bv.nshell * bv.nshell) return;
+  const int sa = (int)(idx / bv.nshell), sb = (int)(idx % bv.nshell);
+  const int la = bv.shell_l[sa], lb = bv.shell_l[sb];
+  const int na = ncart(la), nb = ncart(lb);
+  const double* A = bv.xyz + 3 * bv.shell_atom[sa];
+  const double* B = bv.xyz + 3 * bv.shell_atom[sb];
+  const int oa = bv.shell_coff[sa], ob = bv.shell_coff[sb], nc = bv.ncart;
+  constexpr int NCMAX = ncart(LMAX);
+  constexpr int EMAX = (LMAX + 1) * (LMAX + 3) * (2 * LMAX + 3);  // E up to (la, lb + 2)
+  double sblk[NCMAX * NCMAX], tblk[NCMAX * NCMAX], vblk[NCMAX * NCMAX];
+  for (int x = 0; x < na * nb; ++x) sblk[x] = tblk[x] = vblk[x] = 0.0;
+  const int jm = lb + 2, nt = la + jm + 1;  // kinetic needs j + 2
+  const int se = (la + 1) * (jm + 1) * nt;
+  double E[3 * EMAX];
+  double R[nherm(2 * LMAX)];
+  const double ABx = A[0] - B[0], ABy = A[1] - B[1], ABz = A[2] - B[2];
+  const double rab2 = ABx * ABx + ABy * ABy + ABz * ABz;
+  for (int i = 0; i < g.shell_nprim[sa]; ++i)
+    for (int j = 0; j < g.shell_nprim[sb]; ++j) {
+      const double a = g.exps[g.shell_poff[sa] + i], b = g.exps[g.shell_poff[sb] + j];
+      const double p = a + b, o2p = 0.5 / p;
+      const double cc = g.ncoefs[g.shell_poff[sa] + i] * g.ncoefs[g.shell_poff[sb] + j] * exp(-a * b / p * rab2);
+      double P[3];
+      for (int k = 0; k < 3; ++k) {
+        P[k] = (a * A[k] + b * B[k]) / p;
+        hermite_E_rt<double>(la, jm, P[k] - A[k], P[k] - B[k], o2p, E + k * se);
+      }
+      const double sq = sqrt(3.14159265358979323846 / p);
+#define EE(k, ii, jj, t) E[(k) * se + ((ii) * (jm + 1) + (jj)) * nt + (t)]
+      for (int ia = 0; ia < na; ++ia) {
+        int ax[3];
+        cart_pows_rt(la, ia, ax[0], ax[1], ax[2]);
+        for (int ib = 0; ib < nb; ++ib) {
+          int bx[3];
+          cart_pows_rt(lb, ib, bx[0], bx[1], bx[2]);
+          double s1[3], t1[3];
+          for (int k = 0; k < 3; ++k) {
+            const int ii = ax[k], jj = bx[k];
+            s1[k] = EE(k, ii, jj, 0) * sq;
+            const double sm2 = jj >= 2 ? EE(k, ii, jj - 2, 0) * sq : 0.0;
+            const double sp2 = EE(k, ii, jj + 2, 0) * sq;
+            t1[k] = -0.5 * (jj * (jj - 1) * sm2 - 2.0 * b * (2 * jj + 1) * s1[k] + 4.0 * b * b * sp2);
+          }
+          sblk[ia * nb + ib] += cc * s1[0] * s1[1] * s1[2];
+          tblk[ia * nb + ib] += cc * (t1[0] * s1[1] * s1[2] + s1[0] * t1[1] * s1[2] + s1[0] * s1[1] * t1[2]);
+        }
+      }
+      const int L = la + lb;
+      for (int c = 0; c < bv.natom; ++c) {
+        const double* C = bv.xyz + 3 * c;
+        prim_R_rt<double>(L, p, P[0] - C[0], P[1] - C[1], P[2] - C[2], bv, R);
+        const double pref = -g.charges[c] * 2.0 * 3.14159265358979323846 / p * cc;
+        for (int ia = 0; ia < na; ++ia) {
+          int ax[3];
+          cart_pows_rt(la, ia, ax[0], ax[1], ax[2]);
+          for (int ib = 0; ib < nb; ++ib) {
+            int bx[3];
+            cart_pows_rt(lb, ib, bx[0], bx[1], bx[2]);
+            double s = 0.0;
+            for (int t = 0; t <= ax[0] + bx[0]; ++t)
+              for (int u = 0; u <= ax[1] + bx[1]; ++u)
+                for (int v = 0; v <= ax[2] + bx[2]; ++v)
+                  s += EE(0, ax[0], bx[0], t) * EE(1, ax[1], bx[1], u) * EE(2, ax[2], bx[2], v) * R[hidx_rt(t, u, v)];
+            vblk[ia * nb + ib] += pref * s;
+          }
+        }
+      }
+#undef EE
+    }
+  for (int ia = 0; ia < na; ++ia)
+    for (int ib = 0; ib < nb; ++ib) {
+      const long long o = (long long)(oa + ia) * nc + ob + ib;
+      g.S[o] = sblk[ia * nb + ib];
+      g.T[o] = tblk[ia * nb + ib];
+      g.V[o] = vblk[ia * nb + ib];
+    }
+}
+
+cudaError_t launch_one_electron(const BasisView& bv, const int* shell_nprim, const int* shell_poff,
+                                const double* exps, const double* ncoefs, const double* charges, double* S,
+                                double* T, double* V, cudaStream_t s) {
+  OneElecArgs g{bv, shell_nprim, shell_poff, exps, ncoefs, charges, S, T, V};
+  const long long n = (long long)bv.nshell * bv.nshell;
+  if (n == 0) return cudaSuccess;
+  k_one_electron<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace adft

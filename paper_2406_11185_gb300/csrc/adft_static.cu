@@ -99,11 +99,18 @@ extern "C" int adft_energy_static(const double* D, const double* J, const double
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = nbf < 4 * sms ? nbf : 4 * sms;
+  // Launch errors are checked per launch with cudaPeekAtLastError: an error
+  // that earlier, unrelated work left behind is neither reported as this
+  // call's nor cleared.
+  const cudaError_t before = cudaPeekAtLastError();
   k_energy_rows<<<blocks, 256, 0, s>>>(nbf, D, J, K, partial);
-  k_energy_total<<<1, 1024, 0, s>>>(nbf, partial, E);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_error(std::string("adft_energy_static: ") + cudaGetErrorString(e));
+  cudaError_t e = cudaPeekAtLastError();
+  if (e == cudaSuccess || e == before) {
+    k_energy_total<<<1, 1024, 0, s>>>(nbf, partial, E);
+    e = cudaPeekAtLastError();
+  }
+  if (e != cudaSuccess && e != before) {
+    set_error(std::string("adft_energy_static: launch failed: ") + cudaGetErrorString(e));
     return ADFT_ERR_CUDA;
   }
   return ADFT_OK;

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_warp(JKLaunch a) {
   T* Gsm = Wsm + NHAB * NCD;            // [NAB][NCD]
   T* Eab = Gsm + NAB * NCD;             // [3][EA]
   T* Eprod = Eab + 3 * EA;              // [BT]
-  const long long total = (long long)__ldg(a.prefix + a.nbra);
+  const long long total = (long long)__ldg(a.prefix + a.nseg);
   const BasisView& bv = a.bv;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
   const T* __restrict__ o2pa = Prec<T>::o2p(bv);

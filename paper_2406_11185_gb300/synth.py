@@ -315,12 +315,18 @@ def config(name: str, spherical: bool = True) -> tuple[Molecule, dict]:
     if name == "small_f":  # 2 heavy + 3 H with the f recipe
         m = make_molecule(1601, 2, 3, "4s3p2d1f", "3s2p1d", (1, 8), (0.05, 1e4), (1.9, 2.9), spherical, name)
         return m, dict(thresh=1e-12, split=1e-5, nocc=12, dseed=11601)
+    if name == "small_f3":  # 2 heavy + 3 H with the f recipe, 1-3 primitives (multi-centre f parity)
+        m = make_molecule(1602, 2, 3, "4s3p2d1f", "3s2p1d", (1, 3), (0.05, 1e4), (1.9, 2.9), spherical, name)
+        return m, dict(thresh=1e-12, split=1e-5, nocc=12, dseed=11602)
     if name == "tiny_f":  # 1 heavy + 1 H with the f recipe, 1-3 primitives (gradient pins)
         m = make_molecule(1701, 1, 1, "4s3p2d1f", "3s2p1d", (1, 3), (0.05, 1e4), (1.4, 2.0), spherical, name)
         return m, dict(thresh=1e-12, split=1e-5, nocc=6, dseed=11701)
     if name == "c60":  # 24 heavy + 36 H, ~516 bf, thresh 1e-10, FP64
         m = make_molecule(2001, 24, 36, "3s2p1d", "2s1p", (1, 6), (0.1, 5e3), (1.9, 2.9), spherical, name)
         return m, dict(thresh=1e-10, split=1e-5, nocc=120, dseed=12001)
+    if name == "c240":  # 96 heavy + 144 H, the 60-atom recipe, 2064 bf: the ~2k-function point
+        m = make_molecule(2401, 96, 144, "3s2p1d", "2s1p", (1, 6), (0.1, 5e3), (1.9, 2.9), spherical, name)
+        return m, dict(thresh=1e-10, split=1e-5, nocc=None, dseed=12401)
     if name == "c200":  # 80 heavy + 120 H, f recipe, 4080 bf, mixed
         m = make_molecule(3001, 80, 120, "4s3p2d1f", "3s2p1d", (1, 8), (0.05, 1e4), (1.9, 2.9), spherical, name)
         return m, dict(thresh=1e-12, split=1e-5, nocc=None, dseed=13001)
@@ -341,6 +347,12 @@ def batch_molecules(count: int = 256, base_seed: int = 5000, spherical: bool = T
                           (1.9, 2.9), spherical, f"batch{i}")
         mols.append(m)
     return mols
+
+
+def nuclear_charges(mol: Molecule) -> np.ndarray:
+    """Nuclear charges of the synthetic atoms (a convention of the inputs):
+    heavy atoms are carbon-like (Z = 6), the others hydrogen (Z = 1)."""
+    return np.where(mol.heavy, 6.0, 1.0)
 
 
 def default_nocc(mol: Molecule, nocc) -> int:

@@ -23,4 +23,4 @@ def test_reference_arm_prints_contract_line():
     assert d["value"] > 0 and d["unit"] == "screened quartets/s" and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"].startswith("c60")
+    assert d["config"]["workload"].startswith("c240")

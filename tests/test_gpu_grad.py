@@ -1,6 +1,9 @@
 """GPU nuclear gradient of E_JK against the oracle's analytic gradient,
 central finite differences of the GPU energy (h = 1e-4 bohr, <= 1e-6 Eh/bohr)
 and the zero net force of translation invariance."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -39,6 +42,28 @@ def test_grad_fp64_vs_oracle(name):
           f"net={np.max(np.abs(g.sum(0))):.2e}")
     assert np.max(np.abs(g - gr)) <= 1e-9
     assert np.max(np.abs(g.sum(axis=0))) <= 1e-10 * max(1.0, np.max(np.abs(g)))
+
+
+GOLDEN_F3 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "small_f3_grad.json")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_grad_small_f3_vs_stored_oracle(precision):
+    """f classes with three and four distinct centres: the GPU gradient
+    against the oracle's (stored by tests/golden/make_golden.py, which calls
+    only the oracle)."""
+    ref = json.load(open(GOLDEN_F3))
+    mol, opt, D = _case("small_f3")
+    assert mol.nbf() == ref["nbf"]
+    b = adft.Basis.from_molecule(mol)
+    g = adft.adft_jk_grad(b, torch.from_numpy(D).cuda(), thresh=ref["thresh"], precision=precision,
+                          split=1e-5).cpu().numpy()
+    gr = np.array(ref["grad"])
+    err = np.max(np.abs(g - gr))
+    print(f"small_f3 {precision}: max|dgrad|={err:.2e} max|grad|={np.max(np.abs(gr)):.2e} "
+          f"net={np.max(np.abs(g.sum(0))):.2e}")
+    assert err <= (1e-9 if precision == "fp64" else 1e-5)
+    assert np.max(np.abs(g.sum(axis=0))) <= (1e-10 if precision == "fp64" else 1e-7) * max(1.0, np.max(np.abs(g)))
 
 
 def test_grad_vs_finite_differences_of_gpu_energy():

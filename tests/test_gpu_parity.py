@@ -48,8 +48,10 @@ def _gpu_jk(mol, D, thresh, precision="fp64", split=1e-5):
     return J.cpu().numpy(), K.cpu().numpy(), E, st, b
 
 
+# small_f3: f shells on two heavy atoms and d shells on three H atoms, so f
+# classes with three and four distinct centres are covered
 @pytest.mark.parametrize("name,spherical", [("tiny", True), ("tiny", False), ("small", True), ("tiny_f", True),
-                                            ("tiny_f", False)])
+                                            ("tiny_f", False), ("small_f3", True), ("small_f3", False)])
 def test_fp64_parity(name, spherical):
     mol, opt, D = _case(name, spherical)
     Jr, Kr, Er = _oracle_jk(name, spherical, mol, D, opt["thresh"])
@@ -61,7 +63,8 @@ def test_fp64_parity(name, spherical):
     assert st["quartets_fp32"] == 0 and st["quartets_fp64"] > 0
 
 
-@pytest.mark.parametrize("name,split", [("tiny_f", 1e-5), ("small", 1e-5), ("small", 1e-7)])
+@pytest.mark.parametrize("name,split", [("tiny_f", 1e-5), ("small", 1e-5), ("small", 1e-7), ("small_f3", 1e-5),
+                                        ("small_f3", 1e-3)])
 def test_mixed_precision_energy(name, split):
     mol, opt, D = _case(name)
     Jr, Kr, Er = _oracle_jk(name, True, mol, D, opt["thresh"])
