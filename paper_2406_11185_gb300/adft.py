@@ -35,7 +35,7 @@ EXPORTED = [
     "adft_basis_destroy", "adft_batch_create", "adft_batch_offsets", "adft_batch_grad_offsets", "adft_batch_jk",
     "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version", "adft_autotune",
     "adft_set_tuning", "adft_jk_plan", "adft_energy_static", "adft_batch_last_stats", "adft_batch_last_timings", "adft_batch_autotune",
-    "adft_batch_set_tuning", "adft_alu_peak", "adft_jk_last_class_stats",
+    "adft_batch_set_tuning", "adft_alu_peak", "adft_jk_last_class_stats", "adft_one_electron",
 ]
 
 
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.adft_alu_peak.argtypes = [ip, ip, dp, dp]
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.adft_jk_last_class_stats.argtypes = [vp, i64p, i64p, i64p, dp]
+    L.adft_one_electron.argtypes = [vp, dp, vp, vp, vp, vp]
     L.adft_status_string.argtypes = [ip]
     L.adft_status_string.restype = ctypes.c_char_p
     L.adft_last_error_message.restype = ctypes.c_char_p
@@ -309,6 +310,21 @@ def adft_jk_last_stats(basis: Basis) -> dict:
     st = adft_stats()
     _check(load().adft_jk_last_stats(basis.handle, ctypes.byref(st)), "adft_jk_last_stats")
     return {k: getattr(st, k) for k, _ in adft_stats._fields_}
+
+
+def adft_one_electron(basis: Basis, charges, stream=None, device=None):
+    """Overlap S, kinetic T and nuclear attraction V (CUDA tensors [nbf, nbf])
+    for nuclear charges `charges` (one per atom)."""
+    import torch
+    q = np.ascontiguousarray(np.asarray(charges, dtype=np.float64))
+    if q.shape != (basis.natom,):
+        raise ValueError(f"charges must hold {basis.natom} values")
+    dev = torch.device("cuda") if device is None else device
+    out = [torch.empty((basis.nbf, basis.nbf), dtype=torch.float64, device=dev) for _ in range(3)]
+    vp = ctypes.c_void_p
+    _check(load().adft_one_electron(basis.handle, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    _stream_ptr(stream), *[vp(t.data_ptr()) for t in out]), "adft_one_electron")
+    return tuple(out)
 
 
 def adft_jk_last_class_stats(basis: Basis) -> dict:

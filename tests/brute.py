@@ -69,3 +69,82 @@ def prim_block(ls, centres, exps):
 
     res, err = quad_vec(f, 0.0, 1.0, epsabs=1e-16, epsrel=1e-13, limit=400)
     return res.reshape(len(ca), len(cb), len(cc), len(cd))
+
+
+# ----------------------------------------------------------------------------
+# One-electron integrals by quadrature (no Hermite expansions, no Boys
+# function): every one-dimensional factor is a polynomial times one Gaussian,
+# which Gauss-Hermite quadrature integrates exactly.
+
+def _gauss_1d(polys, expo, centre):
+    """int prod(polys)(x) exp(-expo (x - centre)^2) dx for callables of x."""
+    x = centre + _GX / math.sqrt(expo)
+    v = np.ones_like(x)
+    for f in polys:
+        v = v * f(x)
+    return float(np.sum(_GW * v)) / math.sqrt(expo)
+
+
+def _prim_norm(a, l):
+    df = 1.0
+    for k in range(2 * l - 1, 1, -2):
+        df *= k
+    return (2 * a / math.pi) ** 0.75 * (4 * a) ** (l / 2) / math.sqrt(df)
+
+
+def one_electron_cartesian(mol, charges, what="T"):
+    """Cartesian kinetic (what="T", as 1/2 sum_k <d_k a|d_k b>) or nuclear
+    attraction (what="V", with 1/|r-C| = (2/sqrt(pi)) int_0^inf exp(-t^2 |r-C|^2) dt
+    and the t-integral by adaptive quadrature after t = sqrt(p) u / (1 - u)) matrix
+    of a small molecule."""
+    shells = mol.shells
+    offs, o = [], 0
+    for _, l, _, _ in shells:
+        offs.append(o)
+        o += (l + 1) * (l + 2) // 2
+    M = np.zeros((o, o))
+    atoms = np.asarray(mol.atoms, dtype=float)
+    for sa, (ia_, la, ea, ca) in enumerate(shells):
+        for sb, (ib_, lb, eb, cb) in enumerate(shells):
+            A, B = atoms[ia_], atoms[ib_]
+            for a, c1 in zip(ea, ca):
+                for b, c2 in zip(eb, cb):
+                    w = c1 * c2 * _prim_norm(a, la) * _prim_norm(b, lb)
+                    p = a + b
+                    P = (a * A + b * B) / p
+                    kab = math.exp(-a * b / p * float(np.sum((A - B) ** 2)))
+                    for i, pa in enumerate(cart_powers(la)):
+                        for j, pb in enumerate(cart_powers(lb)):
+                            if what == "T":
+                                S1, D1 = [], []
+                                for k in range(3):
+                                    fa = lambda x, k=k, e=pa[k]: (x - A[k]) ** e
+                                    fb = lambda x, k=k, e=pb[k]: (x - B[k]) ** e
+                                    da = lambda x, k=k, e=pa[k]: (e * (x - A[k]) ** (e - 1) if e else 0.0) - 2 * a * (x - A[k]) ** (e + 1)
+                                    db = lambda x, k=k, e=pb[k]: (e * (x - B[k]) ** (e - 1) if e else 0.0) - 2 * b * (x - B[k]) ** (e + 1)
+                                    S1.append(_gauss_1d([fa, fb], p, P[k]))
+                                    D1.append(_gauss_1d([da, db], p, P[k]))
+                                v = 0.5 * (D1[0] * S1[1] * S1[2] + S1[0] * D1[1] * S1[2] + S1[0] * S1[1] * D1[2])
+                                M[offs[sa] + i, offs[sb] + j] += w * kab * v
+                            else:
+                                tot = 0.0
+                                for C, Z in zip(atoms, charges):
+                                    sc = math.sqrt(p)  # the integrand's scale in t
+
+                                    def f(u):
+                                        if u >= 1.0:
+                                            return 0.0
+                                        t = sc * u / (1.0 - u)
+                                        q = p + t * t
+                                        Rq = (p * P + t * t * C) / q
+                                        g = math.exp(-p * t * t / q * float(np.sum((P - C) ** 2)))
+                                        v = g
+                                        for k in range(3):
+                                            fa = lambda x, k=k, e=pa[k]: (x - A[k]) ** e
+                                            fb = lambda x, k=k, e=pb[k]: (x - B[k]) ** e
+                                            v *= _gauss_1d([fa, fb], q, Rq[k])
+                                        return v * (2.0 / math.sqrt(math.pi)) * sc / (1.0 - u) ** 2
+                                    val, _ = quad_vec(f, 0.0, 1.0, epsabs=1e-15, epsrel=1e-12, limit=400)
+                                    tot += -Z * float(val)
+                                M[offs[sa] + i, offs[sb] + j] += w * kab * tot
+    return M
