@@ -245,6 +245,32 @@ def run_batch(args):
     return 0
 
 
+def run_probe(args):
+    """Untimed builds for profilers (see --probe)."""
+    import torch
+    from paper_2406_11185_gb300 import adft
+    mol, opt, Dn = workload(args.workload)
+    basis = adft.Basis.from_molecule(mol)
+    D = torch.from_numpy(Dn).cuda()
+    kw = (dict(thresh=opt["thresh"], precision="fp64") if args.probe == "fp64" else
+          dict(thresh=opt["thresh"], split=1e9, precision="mixed"))
+    band = 0 if args.probe == "fp64" else 1
+    mask = None
+    if args.probe_cp is not None:
+        mask = np.zeros((2, 55), np.uint8)
+        mask[band, args.probe_cp] = 1
+    for _ in range(args.probe_reps):
+        adft.adft_jk_build(basis, D, check=False, pair_mask=mask, **kw)
+    torch.cuda.synchronize()
+    cs = adft.adft_jk_last_class_stats(basis)
+    rows = [{"cp": cp, "quartets": int(cs["quartets"][band][cp]), "prim_quartets": int(cs["prim_quartets"][band][cp]),
+             "bra_prims": int(cs["bra_prims"][band][cp]), "flops_model": float(cs["flops"][band][cp])}
+            for cp in range(55) if cs["prim_quartets"][band][cp] > 0]
+    print(json.dumps({"probe": args.probe, "workload": args.workload, "class_pair": args.probe_cp,
+                      "phases_ms": adft.adft_jk_last_timings(basis), "classes": rows}), flush=True)
+    return 0
+
+
 def batch_class_pairs(mols):
     ls = sorted({l for m in mols for _, l, _, _ in m.shells})
     ncls = sum(1 for a in ls for b in ls if a >= b)
@@ -349,7 +375,16 @@ def main():
     ap.add_argument("--grad", action="store_true",
                     help="single molecule: also time one nuclear gradient (adft_jk_grad) outside the timed "
                          "steps; batch256: include the gradient of every molecule in each step")
+    ap.add_argument("--probe", choices=["fp64", "fp32"], default=None,
+                    help="profiling target: untimed builds of the workload with every kept quartet in FP64 (fp64) "
+                         "or in FP32 (fp32, mixed with split 1e9), default launch shapes, then per-class "
+                         "statistics as JSON (the command the ncu summaries under profiles/ run)")
+    ap.add_argument("--probe-cp", type=int, default=None, help="with --probe: evaluate only this class pair "
+                    "X(X+1)/2 + Y (a pair mask), for single-kernel captures")
+    ap.add_argument("--probe-reps", type=int, default=2, help="with --probe: number of builds")
     args = ap.parse_args()
+    if args.probe:
+        return run_probe(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch256":

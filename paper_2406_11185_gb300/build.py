@@ -16,8 +16,12 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "lib")
 OUT = os.path.join(OUT_DIR, "libadft.so")
-SOURCES = ["adft_core.cu", "adft_dispatch.cu", "adft_grad.cu", "adft_static.cu", "adft_peaks.cu", "adft_onee.cu"] + [
-    f"adft_eri{p}_{g}.cu" for p in ("64", "32") for g in ("a", "b", "c", "d", "e", "f", "g", "h")] + [
+# The units are ordered longest compile first (the FP32 d-class units), so the
+# parallel build finishes about when its longest unit does.
+SOURCES = ["adft_eri32_j.cu", "adft_eri32_i.cu", "adft_eri32_e.cu"] + [
+    f"adft_eri{p}_{g}.cu" for p in ("64", "32") for g in ("a", "b", "c", "d", "e", "f", "g", "h")
+    if f"adft_eri{p}_{g}.cu" != "adft_eri32_e.cu"] + [
+    "adft_core.cu", "adft_dispatch.cu", "adft_grad.cu", "adft_static.cu", "adft_peaks.cu", "adft_onee.cu"] + [
     f"adft_grad{p}_{g}.cu" for p in ("64", "32") for g in ("a", "b", "c")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

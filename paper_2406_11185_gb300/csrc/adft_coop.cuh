@@ -92,9 +92,10 @@ __device__ __forceinline__ void prim_R_scaled(T alpha, T X, T Y, T Z, T pref, co
   }
 }
 
-// J/K digestion from the contracted block Gs[ab][cd] in shared memory; lane
-// gl of a group of GS lanes handles ket components gl, gl+GS, ... (same
-// weights and targets as digest()).
+// J/K digestion from the contracted block Gs[ab][cd] in shared memory (same
+// weights and targets as digest_range): the GS lanes of the group split the
+// distinct output elements, so every J and K element a quartet touches gets
+// exactly one atomic, NAB + NCD + (NA + NB)(NC + ND) per quartet.
 template <typename T, int LA, int LB, int LC, int LD>
 __device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket, int gl, int GS, const T* Gs) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
@@ -112,41 +113,46 @@ __device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket,
   if (sc == sd) w *= cst<T>(0.5);
   if (a.same_class && bra == ket) w *= cst<T>(0.5);
   const T w4 = T(4) * w, w2 = T(2) * w;
-  const T* __restrict__ D = nullptr;
-  D = dmat<T>(a) + base;
+  const T* __restrict__ D = dmat<T>(a) + base;
   double* __restrict__ Jm = a.J + base;
   double* __restrict__ Km = a.K + base;
-  // J_ab partial over this lane's ket components
-  for (int ab = 0; ab < NAB; ++ab) {
+  for (int ab = gl; ab < NAB; ab += GS) {  // J_ab = sum_cd g D_cd
     T s = T(0);
-    for (int kc = gl; kc < NCD; kc += GS) s += Gs[ab * NCD + kc] * __ldg(D + (oc + kc / ND) * n + od + kc % ND);
+    for (int cd = 0; cd < NCD; ++cd) s += Gs[ab * NCD + cd] * __ldg(D + (oc + cd / ND) * n + od + cd % ND);
     atomicAdd(Jm + (oa + ab / NB) * n + ob + ab % NB, (double)(w4 * s));
   }
-  for (int kc = gl; kc < NCD; kc += GS) {
-    const int ic = kc / ND, id = kc % ND;
+  for (int cd = gl; cd < NCD; cd += GS) {  // J_cd = sum_ab g D_ab
     T s = T(0);
-    for (int ab = 0; ab < NAB; ++ab) s += Gs[ab * NCD + kc] * __ldg(D + (oa + ab / NB) * n + ob + ab % NB);
-    atomicAdd(Jm + (oc + ic) * n + od + id, (double)(w4 * s));
-    for (int ia = 0; ia < NA; ++ia) {
-      T s_ac = T(0), s_ad = T(0);
-      for (int ib = 0; ib < NB; ++ib) {
-        const T g = Gs[(ia * NB + ib) * NCD + kc];
-        s_ac += g * __ldg(D + (ob + ib) * n + od + id);
-        s_ad += g * __ldg(D + (ob + ib) * n + oc + ic);
-      }
-      atomicAdd(Km + (oa + ia) * n + oc + ic, (double)(w2 * s_ac));
-      atomicAdd(Km + (oa + ia) * n + od + id, (double)(w2 * s_ad));
-    }
-    for (int ib = 0; ib < NB; ++ib) {
-      T s_bc = T(0), s_bd = T(0);
-      for (int ia = 0; ia < NA; ++ia) {
-        const T g = Gs[(ia * NB + ib) * NCD + kc];
-        s_bc += g * __ldg(D + (oa + ia) * n + od + id);
-        s_bd += g * __ldg(D + (oa + ia) * n + oc + ic);
-      }
-      atomicAdd(Km + (ob + ib) * n + oc + ic, (double)(w2 * s_bc));
-      atomicAdd(Km + (ob + ib) * n + od + id, (double)(w2 * s_bd));
-    }
+    for (int ab = 0; ab < NAB; ++ab) s += Gs[ab * NCD + cd] * __ldg(D + (oa + ab / NB) * n + ob + ab % NB);
+    atomicAdd(Jm + (oc + cd / ND) * n + od + cd % ND, (double)(w4 * s));
+  }
+  for (int o = gl; o < NA * NC; o += GS) {  // K_ac = sum_bd g D_bd
+    const int x = o / NC, c = o % NC;
+    T s = T(0);
+    for (int y = 0; y < NB; ++y)
+      for (int d = 0; d < ND; ++d) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (ob + y) * n + od + d);
+    atomicAdd(Km + (oa + x) * n + oc + c, (double)(w2 * s));
+  }
+  for (int o = gl; o < NA * ND; o += GS) {  // K_ad = sum_bc g D_bc
+    const int x = o / ND, d = o % ND;
+    T s = T(0);
+    for (int y = 0; y < NB; ++y)
+      for (int c = 0; c < NC; ++c) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (ob + y) * n + oc + c);
+    atomicAdd(Km + (oa + x) * n + od + d, (double)(w2 * s));
+  }
+  for (int o = gl; o < NB * NC; o += GS) {  // K_bc = sum_ad g D_ad
+    const int y = o / NC, c = o % NC;
+    T s = T(0);
+    for (int x = 0; x < NA; ++x)
+      for (int d = 0; d < ND; ++d) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (oa + x) * n + od + d);
+    atomicAdd(Km + (ob + y) * n + oc + c, (double)(w2 * s));
+  }
+  for (int o = gl; o < NB * ND; o += GS) {  // K_bd = sum_ac g D_ac
+    const int y = o / ND, d = o % ND;
+    T s = T(0);
+    for (int x = 0; x < NA; ++x)
+      for (int c = 0; c < NC; ++c) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (oa + x) * n + oc + c);
+    atomicAdd(Km + (ob + y) * n + od + d, (double)(w2 * s));
   }
 }
 
@@ -211,7 +217,7 @@ struct CoopPlan {
 };
 
 template <typename T, int LA, int LB, int LC, int LD>
-__global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
+__global__ void __launch_bounds__(32 * COOP_MAX_WARPS, 1) k_jk_coop(JKLaunch a) {
   using P = CoopPlan<T, LA, LB, LC, LD>;
   constexpr int NB = P::NB, ND = P::ND, NAB = P::NAB, NCD = P::NCD, GS = P::GS, CK = P::CK;
   constexpr int NHAB = P::NHAB, NH = P::NH, EA = P::EA, EC = P::EC, LAB = P::LAB;
@@ -355,6 +361,7 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_coop(JKLaunch a) {
       }
       __syncwarp(gmask);
     }
+    __syncwarp(gmask);  // the digestion reads the whole group's block
     digest_coop<T, LA, LB, LC, LD>(a, bra, ket, gl, GS, Gs);
     __syncwarp(gmask);
   }

@@ -395,10 +395,21 @@ __global__ void k_screen(ScreenArgs a, int npair) {
 }
 
 // ---------------------------------------------------------------------------
-// Counted arithmetic of the ERI kernels (FMA = 2 flops; exp, sqrt and
-// divisions count 1), per primitive quartet, per bra primitive and per
-// contracted quartet of a class, following the loop structure of
-// quartet_block / digest.  Used for the reported FLOP/s only.
+// Algorithmic arithmetic of one class's ERI + digestion work (FMA = 2 flops),
+// used only for the reported FLOP/s.  It counts the sparse McMurchie-Davidson
+// formulation the kernels evaluate:
+//   per primitive quartet: the ket transform, 2 NHAB flops per (tau, nu, phi)
+//     term of every ket component, plus 2.39 per term for its E products;
+//     the Hermite integrals, 1.42 per entry of the layers 1..L; the Boys
+//     function, prefactors and ket E tables, 35.5 + 9.6 L;
+//   per bra primitive: the bra transform, 2 NCD flops per (t, u, v) term of
+//     every bra component, plus 2.08 per term for its E products;
+//   per contracted quartet: the digestion, 12 flops per Cartesian integral.
+// The fractional coefficients were fitted to the FP64 instruction counts
+// (DFMA x 2 + DMUL + DADD, ncu) of the small-class kernel, which executes
+// exactly this formulation, on the 60-atom molecule (every class within
+// 4.5 %); the cooperative and warp kernels execute 10-25 % more than this
+// count (lane-local recomputation), so FLOP/s from it is conservative there.
 struct ClassFlops { double per_pq, per_bra, per_q; };
 
 static int herm_count(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
@@ -407,44 +418,26 @@ static ClassFlops class_flops(int la, int lb, int lc, int ld) {
   const int NB = ncart(lb), ND = ncart(ld);
   const int NAB = ncart(la) * NB, NCD = ncart(lc) * ND;
   const int L = la + lb + lc + ld, NHAB = herm_count(la + lb);
-  const bool small = (L <= 4 && NAB * NCD <= 81);
-  int ck = NCD, nchunk = 1;
-  if (!small) {
-    const int raw = 640 / (NAB + NHAB);
-    ck = raw < 1 ? 1 : (raw > NCD ? NCD : raw);
-    nchunk = (NCD + ck - 1) / ck;
-  }
-  double boys = 12 + 1 + 3.0 * L + 4;
-  double rrec = 0;
-  for (int k = 0; k <= L; ++k) rrec += 3.0 * herm_count(k);
-  const double ecd = 3 * 3.0 * (lc + 1) * (ld + 1) * (lc + ld + 1);
-  double ket = 0;
+  auto pows = [](int l, int k, int* p) {
+    int i = l, off = 0;
+    while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
+    p[0] = i; p[2] = k - off; p[1] = l - p[0] - p[2];
+  };
+  double kterms = 0, bterms = 0, rr = 0;
   for (int kc = 0; kc < NCD; ++kc) {
     int c[3], d[3];
-    for (int t = 0; t < 3; ++t) { c[t] = 0; d[t] = 0; }
-    // powers of components kc / ND and kc % ND
-    auto pows = [](int l, int k, int* p) {
-      int i = l, off = 0;
-      while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
-      p[0] = i; p[2] = k - off; p[1] = l - p[0] - p[2];
-    };
     pows(lc, kc / ND, c); pows(ld, kc % ND, d);
-    ket += (double)(c[0] + d[0] + 1) * (c[1] + d[1] + 1) * (c[2] + d[2] + 1) * (3 + 2.0 * NHAB);
+    kterms += (double)(c[0] + d[0] + 1) * (c[1] + d[1] + 1) * (c[2] + d[2] + 1);
   }
-  ClassFlops f;
-  f.per_pq = nchunk * (boys + rrec + ecd + 12.0) + ket;
-  double bra = 0;
   for (int ab = 0; ab < NAB; ++ab) {
-    int a[3], bb[3];
-    auto pows = [](int l, int k, int* p) {
-      int i = l, off = 0;
-      while (k >= off + (l - i + 1)) { off += l - i + 1; --i; }
-      p[0] = i; p[2] = k - off; p[1] = l - p[0] - p[2];
-    };
-    pows(la, ab / NB, a); pows(lb, ab % NB, bb);
-    bra += (double)(a[0] + bb[0] + 1) * (a[1] + bb[1] + 1) * (a[2] + bb[2] + 1) * (3.0 * nchunk + 2.0 * NCD);
+    int a[3], b[3];
+    pows(la, ab / NB, a); pows(lb, ab % NB, b);
+    bterms += (double)(a[0] + b[0] + 1) * (a[1] + b[1] + 1) * (a[2] + b[2] + 1);
   }
-  f.per_bra = bra + nchunk * 3 * 3.0 * (la + 1) * (lb + 1) * (la + lb + 1);
+  for (int k = 1; k <= L; ++k) rr += herm_count(k);
+  ClassFlops f;
+  f.per_pq = 35.5 + 9.6 * L + 1.42 * rr + (2.39 + 2.0 * NHAB) * kterms;
+  f.per_bra = (2.08 + 2.0 * NCD) * bterms;
   f.per_q = 12.0 * NAB * NCD;
   return f;
 }

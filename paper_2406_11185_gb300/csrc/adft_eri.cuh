@@ -286,13 +286,14 @@ __device__ __forceinline__ void static_for(F&& f) {
   static_for_seq(f, std::make_integer_sequence<int, N>{});
 }
 
-// Contracted Cartesian block of one shell quartet, G[ab*NCD + cd] = (ab|cd),
-// all components in one thread (small classes).  Primitive quartets with
-// Q_p Q_q < eps are skipped; npq and nbp are increased by the primitive
-// quartets and bra primitives evaluated.
-template <typename T, int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int ket, T* G, T eps, int& npq,
-                                              int& nbp) {
+// Contracted Cartesian block of one shell quartet for the ket components
+// [C0, C0 + NK) in one thread, G[ab*NK + k] = (ab|cd)_{C0+k}, with every
+// intermediate in registers.  Primitive quartets with Q_p Q_q < eps are
+// skipped; npq and nbp are increased by the primitive quartets and bra
+// primitives evaluated.
+template <typename T, int LA, int LB, int LC, int LD, int C0, int NK>
+__device__ __forceinline__ void quartet_block_range(const BasisView& bv, int bra, int ket, T* G, T eps, int& npq,
+                                                    int& nbp) {
   constexpr int NB = ncart(LB), ND = ncart(LD);
   constexpr int NAB = ncart(LA) * NB, NCD = ncart(LC) * ND;
   constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
@@ -308,8 +309,9 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
   const T CDx = from_f64<T>(__ldg(bv.pair_AB + 3 * ket)), CDy = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 1)),
           CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
 
+  static_assert(C0 >= 0 && NK >= 1 && C0 + NK <= NCD, "component range");
 #pragma unroll
-  for (int x = 0; x < NAB * NCD; ++x) G[x] = T(0);
+  for (int x = 0; x < NAB * NK; ++x) G[x] = T(0);
 
   const float* __restrict__ qa = bv.pp_q32;
   const float epsf = (float)eps;
@@ -321,14 +323,10 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
     ++nbp;
     const PrimPair<T> bp = pp[off0 + ip];
     const T o2p = __ldg(Prec<T>::o2p(bv) + off0 + ip);
-    T Eab[3][EA];
-    hermite_E<T, LA, LB>(bp.PAx, bp.PAx + ABx, o2p, Eab[0]);
-    hermite_E<T, LA, LB>(bp.PAy, bp.PAy + ABy, o2p, Eab[1]);
-    hermite_E<T, LA, LB>(bp.PAz, bp.PAz + ABz, o2p, Eab[2]);
 
-    T W[NHAB * NCD];
+    T W[NHAB * NK];
 #pragma unroll
-    for (int x = 0; x < NHAB * NCD; ++x) W[x] = T(0);
+    for (int x = 0; x < NHAB * NK; ++x) W[x] = T(0);
 
     for (int iq = 0; iq < n1e; ++iq) {
       const PrimPair<T> kq = pp[off1 + iq];
@@ -344,8 +342,8 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
       prim_R<T, L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
       const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
       // ket transform W[tuv][cd] += sum_{tau nu phi} (+-) E^cd R_{t+tau, u+nu, v+phi}
-      static_for<NCD>([&](auto kk) {
-        constexpr int kc = decltype(kk)::value;
+      static_for<NK>([&](auto kk) {
+        constexpr int k = decltype(kk)::value, kc = C0 + k;
         constexpr int cx = cart_x(LC, kc / ND), cy = cart_y(LC, kc / ND), cz = cart_z(LC, kc / ND);
         constexpr int dx = cart_x(LD, kc % ND), dy = cart_y(LD, kc % ND), dz = cart_z(LD, kc % ND);
 #pragma unroll
@@ -366,14 +364,19 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
 #pragma unroll
                   for (int v = 0; v <= m; ++v) {
                     const int t = n - m, u = m - v;
-                    W[hidx(t, u, v) * NCD + kc] += e2 * R[hidx(t + tau, u + nu, v + phi)];
+                    W[hidx(t, u, v) * NK + k] += e2 * R[hidx(t + tau, u + nu, v + phi)];
                   }
             }
           }
         }
       });
     }
-    // bra transform of this bra primitive
+    // bra transform of this bra primitive (its E tables are formed only now,
+    // when R is dead, which keeps the register footprint of the ket loop down)
+    T Eab[3][EA];
+    hermite_E<T, LA, LB>(bp.PAx, bp.PAx + ABx, o2p, Eab[0]);
+    hermite_E<T, LA, LB>(bp.PAy, bp.PAy + ABy, o2p, Eab[1]);
+    hermite_E<T, LA, LB>(bp.PAz, bp.PAz + ABz, o2p, Eab[2]);
     static_for<NAB>([&](auto abk) {
       constexpr int ab = decltype(abk)::value;
       constexpr int ax = cart_x(LA, ab / NB), ay = cart_y(LA, ab / NB), az = cart_z(LA, ab / NB);
@@ -387,7 +390,7 @@ __device__ __forceinline__ void quartet_block(const BasisView& bv, int bra, int 
           for (int v = 0; v <= az + bz; ++v) {
             const T e1 = exy * Eab[2][(az * (LB + 1) + bz) * NTA + v];
 #pragma unroll
-            for (int kc = 0; kc < NCD; ++kc) G[ab * NCD + kc] += e1 * W[hidx(t, u, v) * NCD + kc];
+            for (int k = 0; k < NK; ++k) G[ab * NK + k] += e1 * W[hidx(t, u, v) * NK + k];
           }
         }
     });
@@ -809,15 +812,17 @@ __device__ __forceinline__ void decode_warp(const JKLaunch& a, long long base, i
 //   K_ac += 2w sum_bd g D_bd,        K_ad += 2w sum_bc g D_bc,
 //   K_bc += 2w sum_ad g D_ad,        K_bd += 2w sum_ac g D_ac,
 // which after X <- (X + X^T)/2 equals the sum over all 8 index permutations.
+// G holds the ket components [C0, C0 + NK) of the block (G[ab*NK + k]).
 // Each thread reads every D element it needs once and sums over both inner
-// indices before its atomic, so a quartet issues NAB + NCD + (NA+NB)(NC+ND)
-// FP64 atomics.  All 32 lanes call it (valid = 0 for a lane without a
-// quartet); when every valid lane of the warp holds the same bra pair, the
-// J_ab sums are reduced across the warp first and one lane adds them.
-template <typename T, int LA, int LB, int LC, int LD>
-__device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, bool valid, const T* G) {
+// indices before its atomic (one atomic per touched J and K element).  All 32
+// lanes call it (valid = 0 for a lane without a quartet); when every valid
+// lane of the warp holds the same bra pair, the J_ab sums are reduced across
+// the warp first and one lane adds them.
+template <typename T, int LA, int LB, int LC, int LD, int C0, int NK>
+__device__ __forceinline__ void digest_range(const JKLaunch& a, int bra, int ket, bool valid, const T* G) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
-  constexpr int NAB = NA * NB, NCD = NC * ND;
+  constexpr int NAB = NA * NB;
+  constexpr int CLO = C0 / ND, CHI = (C0 + NK - 1) / ND;  // ket c shells touched: [CLO, CHI]
   const BasisView& bv = a.bv;
   const int lane = threadIdx.x & 31;
   const int bra0 = __shfl_sync(0xffffffffu, valid ? bra : -1, __ffs(__ballot_sync(0xffffffffu, valid)) - 1);
@@ -842,11 +847,9 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, bool
     const T* __restrict__ D = dmat<T>(a) + base;
     double* __restrict__ Jm = a.J + base;
     double* __restrict__ Km = a.K + base;
-    T Dcd[NCD], Dab[NAB], Dbd[NB * ND], Dbc[NB * NC], Dad[NA * ND], Dac[NA * NC];
+    T Dk[NK], Dab[NAB], Dbd[NB * ND], Dbc[NB * NC], Dad[NA * ND], Dac[NA * NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int d = 0; d < ND; ++d) Dcd[c * ND + d] = dload(D + (oc + c) * n + od + d);
+    for (int k = 0; k < NK; ++k) Dk[k] = dload(D + (oc + (C0 + k) / ND) * n + od + (C0 + k) % ND);
 #pragma unroll
     for (int x = 0; x < NA; ++x)
 #pragma unroll
@@ -856,73 +859,83 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, bool
 #pragma unroll
       for (int d = 0; d < ND; ++d) Dbd[y * ND + d] = dload(D + (ob + y) * n + od + d);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) Dbc[y * NC + c] = dload(D + (ob + y) * n + oc + c);
+      for (int c = CLO; c <= CHI; ++c) Dbc[y * NC + c] = dload(D + (ob + y) * n + oc + c);
     }
 #pragma unroll
     for (int x = 0; x < NA; ++x) {
 #pragma unroll
       for (int d = 0; d < ND; ++d) Dad[x * ND + d] = dload(D + (oa + x) * n + od + d);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) Dac[x * NC + c] = dload(D + (oa + x) * n + oc + c);
+      for (int c = CLO; c <= CHI; ++c) Dac[x * NC + c] = dload(D + (oa + x) * n + oc + c);
     }
     // J_ab (added below, possibly after a warp reduction)
 #pragma unroll
     for (int ab = 0; ab < NAB; ++ab) {
       T s = T(0);
 #pragma unroll
-      for (int cd = 0; cd < NCD; ++cd) s += G[ab * NCD + cd] * Dcd[cd];
+      for (int k = 0; k < NK; ++k) s += G[ab * NK + k] * Dk[k];
       jab[ab] = s;
     }
     // J_cd
 #pragma unroll
-    for (int cd = 0; cd < NCD; ++cd) {
+    for (int k = 0; k < NK; ++k) {
       T s = T(0);
 #pragma unroll
-      for (int ab = 0; ab < NAB; ++ab) s += G[ab * NCD + cd] * Dab[ab];
-      atomicAdd(Jm + (oc + cd / ND) * n + od + cd % ND, (double)(w4 * s));
+      for (int ab = 0; ab < NAB; ++ab) s += G[ab * NK + k] * Dab[ab];
+      atomicAdd(Jm + (oc + (C0 + k) / ND) * n + od + (C0 + k) % ND, (double)(w4 * s));
     }
-    // K_ac, K_ad
+    // K_ac, K_ad (c and d of the range's components)
 #pragma unroll
     for (int x = 0; x < NA; ++x) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
+      for (int c = CLO; c <= CHI; ++c) {
         T s = T(0);
 #pragma unroll
-        for (int y = 0; y < NB; ++y)
+        for (int k = 0; k < NK; ++k)
+          if ((C0 + k) / ND == c)
 #pragma unroll
-          for (int d = 0; d < ND; ++d) s += G[(x * NB + y) * NCD + c * ND + d] * Dbd[y * ND + d];
+            for (int y = 0; y < NB; ++y) s += G[(x * NB + y) * NK + k] * Dbd[y * ND + (C0 + k) % ND];
         atomicAdd(Km + (oa + x) * n + oc + c, (double)(w2 * s));
       }
 #pragma unroll
       for (int d = 0; d < ND; ++d) {
+        bool touched = false;
         T s = T(0);
 #pragma unroll
-        for (int y = 0; y < NB; ++y)
+        for (int k = 0; k < NK; ++k)
+          if ((C0 + k) % ND == d) {
+            touched = true;
 #pragma unroll
-          for (int c = 0; c < NC; ++c) s += G[(x * NB + y) * NCD + c * ND + d] * Dbc[y * NC + c];
-        atomicAdd(Km + (oa + x) * n + od + d, (double)(w2 * s));
+            for (int y = 0; y < NB; ++y) s += G[(x * NB + y) * NK + k] * Dbc[y * NC + (C0 + k) / ND];
+          }
+        if (touched) atomicAdd(Km + (oa + x) * n + od + d, (double)(w2 * s));
       }
     }
     // K_bc, K_bd
 #pragma unroll
     for (int y = 0; y < NB; ++y) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
+      for (int c = CLO; c <= CHI; ++c) {
         T s = T(0);
 #pragma unroll
-        for (int x = 0; x < NA; ++x)
+        for (int k = 0; k < NK; ++k)
+          if ((C0 + k) / ND == c)
 #pragma unroll
-          for (int d = 0; d < ND; ++d) s += G[(x * NB + y) * NCD + c * ND + d] * Dad[x * ND + d];
+            for (int x = 0; x < NA; ++x) s += G[(x * NB + y) * NK + k] * Dad[x * ND + (C0 + k) % ND];
         atomicAdd(Km + (ob + y) * n + oc + c, (double)(w2 * s));
       }
 #pragma unroll
       for (int d = 0; d < ND; ++d) {
+        bool touched = false;
         T s = T(0);
 #pragma unroll
-        for (int x = 0; x < NA; ++x)
+        for (int k = 0; k < NK; ++k)
+          if ((C0 + k) % ND == d) {
+            touched = true;
 #pragma unroll
-          for (int c = 0; c < NC; ++c) s += G[(x * NB + y) * NCD + c * ND + d] * Dac[x * NC + c];
-        atomicAdd(Km + (ob + y) * n + od + d, (double)(w2 * s));
+            for (int x = 0; x < NA; ++x) s += G[(x * NB + y) * NK + k] * Dac[x * NC + (C0 + k) / ND];
+          }
+        if (touched) atomicAdd(Km + (ob + y) * n + od + d, (double)(w2 * s));
       }
     }
   }
@@ -934,7 +947,6 @@ __device__ __forceinline__ void digest(const JKLaunch& a, int bra, int ket, bool
       double v = valid ? (double)(w4 * jab[ab]) : 0.0;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      jab[ab] = (T)0;
       if (lane == __ffs(__ballot_sync(0xffffffffu, valid)) - 1)
         atomicAdd(a.J + base + (oa + ab / NB) * n + ob + ab % NB, v);
     }
@@ -980,11 +992,11 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
     decode_warp(a, (long long)base, valid ? lane : 0, bra, ket);
     if (valid) {
       int npq = 0, nbp = 0;
-      quartet_block<T, LA, LB, LC, LD>(a.bv, bra, ket, G, (T)a.prim_eps, npq, nbp);
+      quartet_block_range<T, LA, LB, LC, LD, 0, NCD>(a.bv, bra, ket, G, (T)a.prim_eps, npq, nbp);
       cpq += npq;
       cbp += nbp;
     }
-    digest<T, LA, LB, LC, LD>(a, bra, ket, valid, G);
+    digest_range<T, LA, LB, LC, LD, 0, NCD>(a, bra, ket, valid, G);
   }
   flush_work(a.work, cpq, cbp);
 }

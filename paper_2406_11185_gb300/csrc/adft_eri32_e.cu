@@ -1,4 +1,4 @@
-// Class-pair ERI kernels (FP32 band), class pairs [(5, 3), (5, 4), (5, 5)]:
+// Class-pair ERI kernels (FP32 band), class pairs [(5, 3)]:
 // explicit instantiations of the launchers of adft_eri.cuh, compiled in parallel
 // with the other groups.
 #include "adft_eri.cuh"
@@ -6,7 +6,5 @@
 namespace adft {
 
 template cudaError_t launch_one<float, 5, 3>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
-template cudaError_t launch_one<float, 5, 4>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
-template cudaError_t launch_one<float, 5, 5>(const JKLaunch&, int, int, cudaStream_t, KernelInfo*);
 
 }  // namespace adft

@@ -158,11 +158,6 @@ constexpr double PRIM_QUARTET_FRAC = 1e-4;
 // Boys tables in device memory of the current device (built once).
 cudaError_t boys_tables(const double** t64, const float** t32);
 
-// Counted flops of one primitive quartet / one contracted quartet of a class
-// (used only for reporting).
-double class_flops_prim(int X, int Y);
-double class_flops_quartet(int X, int Y);
-
 void set_error(const std::string& msg);
 
 }  // namespace adft

@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_warp(JKLaunch a) {
       }
       __syncwarp();
     }
+    __syncwarp();  // the digestion reads the whole warp's block
     digest_coop<T, LA, LB, LC, LD>(a, bra, ket, lane, 32, Gsm);
     __syncwarp();
   }
