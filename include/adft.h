@@ -91,7 +91,9 @@ typedef struct {
 } adft_shell;
 
 typedef struct {
-  double thresh;   /* Schwarz threshold (>= 0): skip iff Q_ab Q_cd < thresh */
+  double thresh;   /* Schwarz threshold: skip iff Q_ab Q_cd < thresh.  Must be >= 1e-12
+                      (ADFT_ERR_ARG otherwise): basis creation drops primitive pairs
+                      whose bound product is <= 1e-15, i.e. at most 1e-3 thresh. */
   double split;    /* mixed modes only: FP64 band iff Q_ab Q_cd >= split */
   int precision;   /* ADFT_PREC_FP64 or ADFT_PREC_MIXED */
   int check;       /* 1: validate D on the device, synchronise the stream and

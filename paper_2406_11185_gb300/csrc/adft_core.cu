@@ -825,6 +825,13 @@ static int finish_check(adft_basis* b, const adft_opts* o, cudaStream_t s) {
 static int check_opts(const adft_opts* o) {
   if (!o) { set_error("opts is NULL"); return ADFT_ERR_ARG; }
   if (!(o->thresh >= 0.0) || !isfinite(o->thresh)) { set_error("thresh must be finite and >= 0"); return ADFT_ERR_ARG; }
+  // Basis creation drops primitive pairs whose bound product is at most
+  // PRIM_EPS = 1e-15; that stays within 1e-3 of the threshold only for
+  // thresh >= 1e-12, so smaller thresholds (including 0) cannot be honoured.
+  if (o->thresh < 1e-12) {
+    set_error("thresh must be >= 1e-12 (primitive pairs with bound products <= 1e-15 are dropped at basis creation)");
+    return ADFT_ERR_ARG;
+  }
   if (o->precision != ADFT_PREC_FP64 && o->precision != ADFT_PREC_MIXED) {
     set_error("precision must be ADFT_PREC_FP64 or ADFT_PREC_MIXED");
     return ADFT_ERR_ARG;

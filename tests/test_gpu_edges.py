@@ -80,3 +80,17 @@ def test_edge_molecules_vs_oracle(kind):
     assert np.max(np.abs(g - gr)) <= TOL_GRAD
     if kind == "single_atom":  # the energy cannot depend on the position of a lone atom
         assert np.max(np.abs(g)) <= 1e-10
+
+
+def test_threshold_below_primitive_drop_rejected():
+    """Primitive pairs with bound products <= 1e-15 are dropped when the basis
+    is created, so a threshold below 1e-12 (or 0) is refused, not silently
+    approximated."""
+    mol, opt = synth.config("tiny")
+    D = torch.from_numpy(synth.make_density(mol, opt["nocc"], opt["dseed"])).cuda()
+    b = adft.Basis.from_molecule(mol)
+    for thr in (0.0, 1e-13):
+        with pytest.raises(adft.AdftError) as e:
+            adft.adft_jk_build(b, D, thresh=thr)
+        assert e.value.status == adft.ADFT_ERR_ARG and "1e-12" in str(e.value)
+    adft.adft_jk_build(b, D, thresh=1e-12)  # the smallest accepted threshold
