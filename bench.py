@@ -281,9 +281,27 @@ def run_probe(args):
     mol, opt, Dn = workload(args.workload)
     basis = adft.Basis.from_molecule(mol)
     D = torch.from_numpy(Dn).cuda()
-    kw = (dict(thresh=opt["thresh"], precision="fp64") if args.probe == "fp64" else
-          dict(thresh=opt["thresh"], split=1e9, precision="mixed"))
+    split = opt["split"] if args.split is None else args.split
+    kw = {"fp64": dict(thresh=opt["thresh"], precision="fp64"),
+          "fp32": dict(thresh=opt["thresh"], split=1e9, precision="mixed"),
+          "mixed": dict(thresh=opt["thresh"], split=split, precision="mixed")}[args.probe]
     band = 0 if args.probe == "fp64" else 1
+    tab = None
+    if args.probe == "mixed":  # the benchmark's launch shapes: autotuned on the 60-atom molecule
+        tname = "c60" if args.workload == "c240" else args.workload
+        tmol, topt, tD = workload(tname)
+        tb = adft.Basis.from_molecule(tmol) if tname != args.workload else basis
+        tab = adft.adft_autotune(tb, torch.from_numpy(tD).cuda(), thresh=topt["thresh"], split=split,
+                                 precision="mixed")
+        adft.adft_set_tuning(basis, tab)
+    if args.probe_variant is not None:
+        if args.probe_cp is None:
+            raise SystemExit("--probe-variant needs --probe-cp")
+        if tab is None:
+            tab = np.full((2, 55), 4, dtype=np.int32)
+        tab[band, args.probe_cp] = tab[band, args.probe_cp] % adft.TUNE_VARIANT_STRIDE + \
+            args.probe_variant * adft.TUNE_VARIANT_STRIDE
+        adft.adft_set_tuning(basis, tab)
     mask = None
     if args.probe_cp is not None:
         mask = np.zeros((2, 55), np.uint8)
@@ -292,11 +310,14 @@ def run_probe(args):
         adft.adft_jk_build(basis, D, check=False, pair_mask=mask, **kw)
     torch.cuda.synchronize()
     cs = adft.adft_jk_last_class_stats(basis)
-    rows = [{"cp": cp, "quartets": int(cs["quartets"][band][cp]), "prim_quartets": int(cs["prim_quartets"][band][cp]),
-             "bra_prims": int(cs["bra_prims"][band][cp]), "flops_model": float(cs["flops"][band][cp])}
-            for cp in range(55) if cs["prim_quartets"][band][cp] > 0]
+    rows = [{"band": bd, "cp": cp, "quartets": int(cs["quartets"][bd][cp]),
+             "prim_quartets": int(cs["prim_quartets"][bd][cp]), "bra_prims": int(cs["bra_prims"][bd][cp]),
+             "flops_model": float(cs["flops"][bd][cp]),
+             "tuning": None if tab is None else int(tab[bd][cp])}
+            for bd in (0, 1) for cp in range(55) if cs["prim_quartets"][bd][cp] > 0]
     print(json.dumps({"probe": args.probe, "workload": args.workload, "class_pair": args.probe_cp,
-                      "phases_ms": adft.adft_jk_last_timings(basis), "classes": rows}), flush=True)
+                      "variant": args.probe_variant, "phases_ms": adft.adft_jk_last_timings(basis),
+                      "classes": rows}), flush=True)
     return 0
 
 
@@ -404,10 +425,13 @@ def main():
     ap.add_argument("--grad", action="store_true",
                     help="single molecule: also time one nuclear gradient (adft_jk_grad) outside the timed "
                          "steps; batch256: include the gradient of every molecule in each step")
-    ap.add_argument("--probe", choices=["fp64", "fp32"], default=None,
+    ap.add_argument("--probe", choices=["fp64", "fp32", "mixed"], default=None,
                     help="profiling target: untimed builds of the workload with every kept quartet in FP64 (fp64) "
-                         "or in FP32 (fp32, mixed with split 1e9), default launch shapes, then per-class "
-                         "statistics as JSON (the command the ncu summaries under profiles/ run)")
+                         "or in FP32 (fp32, mixed with split 1e9), default launch shapes; or the benchmark's "
+                         "mixed build (mixed: the workload's split, launch shapes autotuned as in the benchmark); "
+                         "then per-class statistics as JSON (the command the ncu summaries under profiles/ run)")
+    ap.add_argument("--probe-variant", type=int, default=None, help="with --probe-cp: run that class pair with "
+                    "this kernel variant (adft_set_tuning)")
     ap.add_argument("--probe-cp", type=int, default=None, help="with --probe: evaluate only this class pair "
                     "X(X+1)/2 + Y (a pair mask), for single-kernel captures")
     ap.add_argument("--probe-reps", type=int, default=2, help="with --probe: number of builds")

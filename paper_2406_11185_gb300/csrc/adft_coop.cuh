@@ -92,11 +92,11 @@ __device__ __forceinline__ void prim_R_scaled(T alpha, T X, T Y, T Z, T pref, co
   }
 }
 
-// J/K digestion from the contracted block Gs[ab][cd] in shared memory (same
+// J/K digestion from the contracted block Gs[ab * GSTRIDE + cd] in shared memory (same
 // weights and targets as digest_range): the GS lanes of the group split the
 // distinct output elements, so every J and K element a quartet touches gets
 // exactly one atomic, NAB + NCD + (NA + NB)(NC + ND) per quartet.
-template <typename T, int LA, int LB, int LC, int LD>
+template <typename T, int LA, int LB, int LC, int LD, int GSTRIDE = ncart(LC) * ncart(LD)>
 __device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket, int gl, int GS, const T* Gs) {
   constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   constexpr int NAB = NA * NB, NCD = NC * ND;
@@ -118,40 +118,40 @@ __device__ __forceinline__ void digest_coop(const JKLaunch& a, int bra, int ket,
   double* __restrict__ Km = a.K + base;
   for (int ab = gl; ab < NAB; ab += GS) {  // J_ab = sum_cd g D_cd
     T s = T(0);
-    for (int cd = 0; cd < NCD; ++cd) s += Gs[ab * NCD + cd] * __ldg(D + (oc + cd / ND) * n + od + cd % ND);
+    for (int cd = 0; cd < NCD; ++cd) s += Gs[ab * GSTRIDE + cd] * __ldg(D + (oc + cd / ND) * n + od + cd % ND);
     atomicAdd(Jm + (oa + ab / NB) * n + ob + ab % NB, (double)(w4 * s));
   }
   for (int cd = gl; cd < NCD; cd += GS) {  // J_cd = sum_ab g D_ab
     T s = T(0);
-    for (int ab = 0; ab < NAB; ++ab) s += Gs[ab * NCD + cd] * __ldg(D + (oa + ab / NB) * n + ob + ab % NB);
+    for (int ab = 0; ab < NAB; ++ab) s += Gs[ab * GSTRIDE + cd] * __ldg(D + (oa + ab / NB) * n + ob + ab % NB);
     atomicAdd(Jm + (oc + cd / ND) * n + od + cd % ND, (double)(w4 * s));
   }
   for (int o = gl; o < NA * NC; o += GS) {  // K_ac = sum_bd g D_bd
     const int x = o / NC, c = o % NC;
     T s = T(0);
     for (int y = 0; y < NB; ++y)
-      for (int d = 0; d < ND; ++d) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (ob + y) * n + od + d);
+      for (int d = 0; d < ND; ++d) s += Gs[(x * NB + y) * GSTRIDE + c * ND + d] * __ldg(D + (ob + y) * n + od + d);
     atomicAdd(Km + (oa + x) * n + oc + c, (double)(w2 * s));
   }
   for (int o = gl; o < NA * ND; o += GS) {  // K_ad = sum_bc g D_bc
     const int x = o / ND, d = o % ND;
     T s = T(0);
     for (int y = 0; y < NB; ++y)
-      for (int c = 0; c < NC; ++c) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (ob + y) * n + oc + c);
+      for (int c = 0; c < NC; ++c) s += Gs[(x * NB + y) * GSTRIDE + c * ND + d] * __ldg(D + (ob + y) * n + oc + c);
     atomicAdd(Km + (oa + x) * n + od + d, (double)(w2 * s));
   }
   for (int o = gl; o < NB * NC; o += GS) {  // K_bc = sum_ad g D_ad
     const int y = o / NC, c = o % NC;
     T s = T(0);
     for (int x = 0; x < NA; ++x)
-      for (int d = 0; d < ND; ++d) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (oa + x) * n + od + d);
+      for (int d = 0; d < ND; ++d) s += Gs[(x * NB + y) * GSTRIDE + c * ND + d] * __ldg(D + (oa + x) * n + od + d);
     atomicAdd(Km + (ob + y) * n + oc + c, (double)(w2 * s));
   }
   for (int o = gl; o < NB * ND; o += GS) {  // K_bd = sum_ac g D_ac
     const int y = o / ND, d = o % ND;
     T s = T(0);
     for (int x = 0; x < NA; ++x)
-      for (int c = 0; c < NC; ++c) s += Gs[(x * NB + y) * NCD + c * ND + d] * __ldg(D + (oa + x) * n + oc + c);
+      for (int c = 0; c < NC; ++c) s += Gs[(x * NB + y) * GSTRIDE + c * ND + d] * __ldg(D + (oa + x) * n + oc + c);
     atomicAdd(Km + (ob + y) * n + od + d, (double)(w2 * s));
   }
 }
@@ -272,7 +272,8 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS, 1) k_jk_coop(JKLaunch a) 
       const T o2p = __ldg(o2pa + off0 + ip);
       for (int d = gl; d < 3; d += GS) {  // groups may have fewer than 3 lanes
         const T PA = d == 0 ? bp.PAx : d == 1 ? bp.PAy : bp.PAz;
-        hermite_E<T, LA, LB>(PA, PA + AB[d], o2p, Eab + d * EA);
+        const T ABd = d == 0 ? AB[0] : d == 1 ? AB[1] : AB[2];  // (no dynamic register index)
+        hermite_E<T, LA, LB>(PA, PA + ABd, o2p, Eab + d * EA);
       }
       T W[NHAB * CK];
 #pragma unroll

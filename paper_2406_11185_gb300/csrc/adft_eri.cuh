@@ -610,8 +610,8 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
   T W[S::NW];
   for (int x = 0; x < NAB * CK; ++x) G[x] = T(0);
 
-#pragma unroll 1
   int n1e = n1;
+#pragma unroll 1
   for (int ip = 0; ip < n0; ++ip) {
     if (eps > T(0)) {
       n1e = shrink_kept(bv.pp_q32 + off1, __ldg(bv.pp_q32 + off0 + ip), (float)eps, n1e);
@@ -1105,6 +1105,7 @@ static __global__ void __launch_bounds__(JK_THREADS) k_prim_schwarz(BasisView bv
 
 #include "adft_coop.cuh"
 #include "adft_warp.cuh"
+#include "adft_row.cuh"
 
 // ---------------------------------------------------------------------------
 // dispatch: one launcher per (X, Y) class pair, X >= Y.  The launchers are
@@ -1155,23 +1156,44 @@ cudaError_t launch_one(const JKLaunch& a, int grid, int variant, cudaStream_t s,
     static PerDeviceFlag configured;
     return start(k_jk<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured.current(), 1, s, info);
   } else if constexpr (WarpPlan<T, LA, LB, LC, LD>::fits) {
-    // Both kernels serve these classes and the autotuner picks one.  Variant 0
-    // is the warp kernel in FP64 and the cooperative one in FP32, the faster
-    // choice of each on the 60-atom workload.
+    // Three kernels serve these classes and the autotuner picks one.  Variant
+    // 0 is the warp kernel in FP64 and the cooperative one in FP32, variant 1
+    // the other of the two, variant 2 the row-blocked kernel.
     static_assert(CoopPlan<T, LA, LB, LC, LD>::fits, "warp-kernel classes also need the cooperative kernel");
     using W = WarpPlan<T, LA, LB, LC, LD>;
     using C = CoopPlan<T, LA, LB, LC, LD>;
+    using R = RowPlan<T, LA, LB, LC, LD>;
+    constexpr int nvar = R::fits ? 3 : 2;
     constexpr bool warp_first = sizeof(T) == 8;
+    if constexpr (R::fits) {
+      if (variant == 2) {
+        static PerDeviceFlag configured;
+        return start(k_jk_row<T, LA, LB, LC, LD>, a, grid, 32 * R::WARPS, R::SMEM, configured.current(), nvar, s,
+                     info);
+      }
+    }
     if ((variant == 0) == warp_first) {
       static PerDeviceFlag configured;
-      return start(k_jk_warp<T, LA, LB, LC, LD>, a, grid, 32 * W::WARPS, W::SMEM, configured.current(), 2, s, info);
+      return start(k_jk_warp<T, LA, LB, LC, LD>, a, grid, 32 * W::WARPS, W::SMEM, configured.current(), nvar, s,
+                   info);
     }
     static PerDeviceFlag configured;
-    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), 2, s, info);
+    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), nvar, s, info);
   } else if constexpr (CoopPlan<T, LA, LB, LC, LD>::fits) {
+    // variant 0: the cooperative kernel; variant 1: the row-blocked kernel
+    // where its plan fits
     using C = CoopPlan<T, LA, LB, LC, LD>;
+    using R = RowPlan<T, LA, LB, LC, LD>;
+    constexpr int nvar = R::fits ? 2 : 1;
+    if constexpr (R::fits) {
+      if (variant == 1) {
+        static PerDeviceFlag configured;
+        return start(k_jk_row<T, LA, LB, LC, LD>, a, grid, 32 * R::WARPS, R::SMEM, configured.current(), nvar, s,
+                     info);
+      }
+    }
     static PerDeviceFlag configured;
-    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), 1, s, info);
+    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), nvar, s, info);
   } else {
     static PerDeviceFlag configured;
     return start(k_jk_generic<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured.current(), 1, s, info);

@@ -77,38 +77,47 @@ def test_mixed_precision_energy(name, split):
     assert dj <= 1e-5 and dk <= 1e-5
 
 
-def _two_variant_pairs(b):
-    """Class pairs X(X+1)/2 + Y served by two kernels (warp per quartet and
-    cooperative group): adft_set_tuning accepts variant 1 only there."""
-    found = []
-    for cp in range(55):
-        tab = np.full((2, 55), 2, dtype=np.int32)
-        tab[:, cp] += adft.TUNE_VARIANT_STRIDE
-        try:
-            adft.adft_set_tuning(b, tab)
-            found.append(cp)
-        except adft.AdftError:
-            pass
+def _variant_pairs(b, variant):
+    """Class pairs X(X+1)/2 + Y of each band (0 FP64, 1 FP32) with a kernel
+    variant `variant`: adft_set_tuning rejects a variant past a pair's count.
+    Variant 1 is the warp or cooperative kernel of the pairs served by both
+    (the row-blocked kernel of the pairs served by the cooperative one only),
+    variant 2 the row-blocked kernel of the pairs served by all three."""
+    found = {0: [], 1: []}
+    for band in (0, 1):
+        for cp in range(55):
+            tab = np.full((2, 55), 2, dtype=np.int32)
+            tab[band, cp] += variant * adft.TUNE_VARIANT_STRIDE
+            try:
+                adft.adft_set_tuning(b, tab)
+                found[band].append(cp)
+            except adft.AdftError:
+                pass
     return found
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_alternative_kernel_variant_parity(precision):
+def test_alternative_kernel_variant_parity(variant, precision):
     mol, opt, D = _case("small")
     Jr, Kr, Er = _oracle_jk("small", True, mol, D, opt["thresh"])
     b = adft.Basis.from_molecule(mol)
-    pairs = _two_variant_pairs(b)
-    # (dp|pp), (dp|ds), (dp|dp)
-    assert {12, 13, 14} <= set(pairs), pairs
+    pairs = _variant_pairs(b, variant)
+    # (dp|pp), (dp|ds), (dp|dp) have a second and a third kernel in FP32;
+    # every d-class pair up to (dd|dp) has a second one
+    assert {12, 13, 14} <= set(pairs[1]), pairs
+    if variant == 1:
+        assert {12, 13, 14, 19} <= set(pairs[0]) and {19} <= set(pairs[1]), pairs
     tab = np.full((2, 55), 2, dtype=np.int32)
-    tab[:, pairs] += adft.TUNE_VARIANT_STRIDE
+    for band in (0, 1):
+        tab[band, pairs[band]] += variant * adft.TUNE_VARIANT_STRIDE
     adft.adft_set_tuning(b, tab)
     Dt = torch.from_numpy(D).cuda()
     J, K = adft.adft_jk_build(b, Dt, thresh=opt["thresh"], precision=precision)
     E = adft.adft_jk_energy(b, Dt, thresh=opt["thresh"], precision=precision)
     dj = np.max(np.abs(J.cpu().numpy() - Jr))
     dk = np.max(np.abs(K.cpu().numpy() - Kr))
-    print(f"variant 1 on {pairs} {precision}: max|dJ|={dj:.2e} max|dK|={dk:.2e} |dE|={abs(E - Er):.2e}")
+    print(f"variant {variant} on {pairs} {precision}: max|dJ|={dj:.2e} max|dK|={dk:.2e} |dE|={abs(E - Er):.2e}")
     if precision == "fp64":
         assert dj <= TOL_JK and dk <= TOL_JK and abs(E - Er) <= TOL_E
     else:
