@@ -203,10 +203,12 @@ int adft_jk_last_timings(adft_basis* b, double* ms);
 
 /* Autotuner (per angular-momentum class pair and precision band): times
  * every class-pair kernel of one build of D in each kernel variant that
- * serves the class pair (two, a warp-per-quartet kernel and a cooperative
- * group kernel, for (dp|pp), (dp|ds), (dp|dp); one elsewhere) and with 1, 2, 4 and 8 resident blocks per SM
- * (counts that cannot be resident at once are skipped), and keeps the
- * fastest choice in the handle for later calls.  The J/K accumulators of the
+ * serves the class pair and with 1, 2, 4 and 8 resident blocks per SM.  The
+ * d-class pairs up to (dd|dp) have two to four variants: the cooperative
+ * group kernel, a warp-per-quartet kernel for (dp|pp), (dp|ds), (dp|dp), and
+ * the row-blocked kernel in one or two launch shapes; the other pairs have
+ * one.  Block counts that cannot be resident at once are skipped.  The
+ * fastest choice is kept in the handle for later calls.  The J/K accumulators of the
  * handle are left undefined.
  *   table: host [2][55] ints (band-major: FP64 then FP32; class pair
  *   X(X+1)/2 + Y with class X = l_a(l_a+1)/2 + l_b) or NULL; each entry is

@@ -1155,46 +1155,58 @@ cudaError_t launch_one(const JKLaunch& a, int grid, int variant, cudaStream_t s,
   } else if constexpr (is_small_class(LA, LB, LC, LD)) {
     static PerDeviceFlag configured;
     return start(k_jk<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured.current(), 1, s, info);
-  } else if constexpr (WarpPlan<T, LA, LB, LC, LD>::fits) {
-    // Three kernels serve these classes and the autotuner picks one.  Variant
-    // 0 is the warp kernel in FP64 and the cooperative one in FP32, variant 1
-    // the other of the two, variant 2 the row-blocked kernel.
-    static_assert(CoopPlan<T, LA, LB, LC, LD>::fits, "warp-kernel classes also need the cooperative kernel");
+  } else if constexpr (CoopPlan<T, LA, LB, LC, LD>::fits) {
+    // Up to four kernels serve these classes and the autotuner picks one.
+    // Variant 0 is the warp kernel in FP64 where it exists and the
+    // cooperative one otherwise; variant 1 the other of the two where both
+    // exist; then the row-blocked kernel with the busiest shape (policy 0) and
+    // with the occupancy-aware shape (policy 1), where their plans fit.
     using W = WarpPlan<T, LA, LB, LC, LD>;
     using C = CoopPlan<T, LA, LB, LC, LD>;
-    using R = RowPlan<T, LA, LB, LC, LD>;
-    constexpr int nvar = R::fits ? 3 : 2;
-    constexpr bool warp_first = sizeof(T) == 8;
-    if constexpr (R::fits) {
-      if (variant == 2) {
+    using R0 = RowPlan<T, LA, LB, LC, LD, 0>;
+    using R1 = RowPlan<T, LA, LB, LC, LD, 1>;
+    constexpr bool hw = W::fits, h0 = R0::fits, h1 = R1::fits;
+    constexpr int nvar = 1 + (hw ? 1 : 0) + (h0 ? 1 : 0) + (h1 ? 1 : 0);
+    constexpr bool warp_first = hw && sizeof(T) == 8;
+    int v = variant;
+    if constexpr (hw) {
+      if (v == 0 || v == 1) {
+        if ((v == 0) == warp_first) {
+          static PerDeviceFlag configured;
+          return start(k_jk_warp<T, LA, LB, LC, LD>, a, grid, 32 * W::WARPS, W::SMEM, configured.current(), nvar,
+                       s, info);
+        }
         static PerDeviceFlag configured;
-        return start(k_jk_row<T, LA, LB, LC, LD>, a, grid, 32 * R::WARPS, R::SMEM, configured.current(), nvar, s,
+        return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), nvar, s,
                      info);
       }
-    }
-    if ((variant == 0) == warp_first) {
-      static PerDeviceFlag configured;
-      return start(k_jk_warp<T, LA, LB, LC, LD>, a, grid, 32 * W::WARPS, W::SMEM, configured.current(), nvar, s,
-                   info);
-    }
-    static PerDeviceFlag configured;
-    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), nvar, s, info);
-  } else if constexpr (CoopPlan<T, LA, LB, LC, LD>::fits) {
-    // variant 0: the cooperative kernel; variant 1: the row-blocked kernel
-    // where its plan fits
-    using C = CoopPlan<T, LA, LB, LC, LD>;
-    using R = RowPlan<T, LA, LB, LC, LD>;
-    constexpr int nvar = R::fits ? 2 : 1;
-    if constexpr (R::fits) {
-      if (variant == 1) {
+      v -= 2;
+    } else {
+      if (v == 0) {
         static PerDeviceFlag configured;
-        return start(k_jk_row<T, LA, LB, LC, LD>, a, grid, 32 * R::WARPS, R::SMEM, configured.current(), nvar, s,
+        return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), nvar, s,
                      info);
       }
+      v -= 1;
     }
-    static PerDeviceFlag configured;
-    return start(k_jk_coop<T, LA, LB, LC, LD>, a, grid, 32 * C::WARPS, C::SMEM, configured.current(), nvar, s, info);
+    if constexpr (h0) {
+      if (v == 0) {
+        static PerDeviceFlag configured;
+        return start(k_jk_row<T, LA, LB, LC, LD, 0>, a, grid, 32 * R0::WARPS, R0::SMEM, configured.current(), nvar,
+                     s, info);
+      }
+      --v;
+    }
+    if constexpr (h1) {
+      if (v == 0) {
+        static PerDeviceFlag configured;
+        return start(k_jk_row<T, LA, LB, LC, LD, 1>, a, grid, 32 * R1::WARPS, R1::SMEM, configured.current(), nvar,
+                     s, info);
+      }
+    }
+    return cudaErrorInvalidValue;  // variant past the count (adft_set_tuning rejects it)
   } else {
+    static_assert(!WarpPlan<T, LA, LB, LC, LD>::fits, "warp-kernel classes also need the cooperative kernel");
     static PerDeviceFlag configured;
     return start(k_jk_generic<T, LA, LB, LC, LD>, a, grid, JK_THREADS, 0, configured.current(), 1, s, info);
   }

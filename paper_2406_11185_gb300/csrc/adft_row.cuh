@@ -211,7 +211,48 @@ __host__ __device__ constexpr int row_slots(int gs, int ksize, int nhab, int ncd
   return 1;
 }
 
-template <typename T, int LA, int LB, int LC, int LD>
+// Occupancy-aware shape (policy 1): the d-class kernels are latency-bound at
+// a few warps per SM, so this policy scores a shape by busy fraction x the
+// warps per SM that its shared memory (228 KB per SM, the slots taken as
+// large as 4 resident warps allow) and an estimate of its registers (rows +
+// 120 per thread) let reside, up to 8.
+struct RowShape3 {
+  int gs, rpl, sl;
+};
+__host__ __device__ constexpr RowShape3 row_shape_occ(int nhab, int row_regs, int cap, int ksize, int ncdp, int ec,
+                                                      int nab, int nh, int ea, int bt, int vw, int tsize) {
+  RowShape3 best{32, (nhab + 31) / 32, 1};
+  double best_s = -1.0;
+  for (int gs = 1; gs <= 32; ++gs) {
+    const int rpl = (nhab + gs - 1) / gs;
+    if (rpl * row_regs > cap) continue;
+    const int ngw = 32 / gs;
+    const double u = (double)(ngw * gs) / 32.0 * (double)nhab / (double)(gs * rpl);
+    const int opts[4] = {COOP_SLOT_CAP, 4, 2, 1};
+    int sl = 1, wsm = 0;
+    for (int i = 0; i < 4; ++i) {
+      if (opts[i] > gs) continue;
+      sl = opts[i];
+      wsm = (228 * 1024) / (ngw * row_group(sl, ksize, nhab, ncdp, ec, nab, nh, ea, bt, vw) * tsize);
+      if (wsm >= 4) break;
+    }
+    const int regs = rpl * row_regs + 120 > 255 ? 255 : rpl * row_regs + 120;
+    const int wreg = 65536 / (32 * regs);
+    int occ = wsm < wreg ? wsm : wreg;
+    if (occ > 8) occ = 8;
+    const double score = u * (double)occ;
+    if (score > best_s + 1e-9 || (score > best_s - 1e-9 && rpl > best.rpl)) {
+      best_s = score;
+      best = RowShape3{gs, rpl, sl};
+    }
+  }
+  return best;
+}
+
+// POLICY 0: the busiest shape (row_shape, row_slots); POLICY 1: the
+// occupancy-aware one (row_shape_occ).  A policy-1 plan that equals the
+// policy-0 plan does not fit, so no kernel is compiled twice.
+template <typename T, int LA, int LB, int LC, int LD, int POLICY = 0>
 struct RowPlan {
   static constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
   static constexpr int NAB = NA * NB, NCD = NC * ND;
@@ -224,9 +265,14 @@ struct RowPlan {
   static constexpr int NCDP = (NCD + VW - 1) / VW * VW;
   static constexpr int ROW_REGS = NCD * (int)(sizeof(T) / 4) + 2 * (LCD + 1);
   static constexpr int REG_CAP = 104;  // registers of the rows of one lane
-  static constexpr RowShape SHAPE = row_shape(NHAB, ROW_REGS, REG_CAP);
-  static constexpr int GS = SHAPE.gs, RPL = SHAPE.rpl, NGW = 32 / GS;
-  static constexpr int SL = row_slots(GS, KSIZE, NHAB, NCDP, EC, NAB, NH, EA, BT, VW, (int)sizeof(T));
+  static constexpr RowShape SHAPE0 = row_shape(NHAB, ROW_REGS, REG_CAP);
+  static constexpr int SL0 = row_slots(SHAPE0.gs, KSIZE, NHAB, NCDP, EC, NAB, NH, EA, BT, VW, (int)sizeof(T));
+  static constexpr RowShape3 SHAPE1 =
+      row_shape_occ(NHAB, ROW_REGS, REG_CAP, KSIZE, NCDP, EC, NAB, NH, EA, BT, VW, (int)sizeof(T));
+  static constexpr int GS = POLICY == 0 ? SHAPE0.gs : SHAPE1.gs;
+  static constexpr int RPL = POLICY == 0 ? SHAPE0.rpl : SHAPE1.rpl;
+  static constexpr int SL = POLICY == 0 ? SL0 : SHAPE1.sl;
+  static constexpr int NGW = 32 / GS;
   static constexpr int WE = row_we(SL, NHAB, NCDP, EC, VW);
   static constexpr int RSZ = row_pad(SL * NH, VW), EASZ = row_pad(3 * EA, VW);
   static constexpr int GROUP = row_group(SL, KSIZE, NHAB, NCDP, EC, NAB, NH, EA, BT, VW);
@@ -234,14 +280,16 @@ struct RowPlan {
   static constexpr int WFIT = COOP_SMEM_BUDGET / WARP_BYTES;
   static constexpr int WARPS = WFIT > COOP_MAX_WARPS ? COOP_MAX_WARPS : WFIT;
   static constexpr int SMEM = WARPS * WARP_BYTES;
+  static constexpr bool distinct =
+      POLICY == 0 || !(SHAPE1.gs == SHAPE0.gs && SHAPE1.rpl == SHAPE0.rpl && SHAPE1.sl == SL0);
   // the classes of the cooperative kernel (up to d shells) with at least two
   // warps per block and rows within the register cap
-  static constexpr bool fits = WARPS >= 2 && RPL * ROW_REGS <= REG_CAP && LA <= 2 && LC <= 2;
+  static constexpr bool fits = WARPS >= 2 && RPL * ROW_REGS <= REG_CAP && LA <= 2 && LC <= 2 && distinct;
 };
 
-template <typename T, int LA, int LB, int LC, int LD>
-__global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_row(JKLaunch a) {
-  using P = RowPlan<T, LA, LB, LC, LD>;
+template <typename T, int LA, int LB, int LC, int LD, int POLICY>
+__global__ void __launch_bounds__(32 * COOP_MAX_WARPS, 1) k_jk_row(JKLaunch a) {
+  using P = RowPlan<T, LA, LB, LC, LD, POLICY>;
   using RV = RowVec<T>;
   using V = typename RV::V;
   constexpr int NAB = P::NAB, NCD = P::NCD, NCDP = P::NCDP, NHAB = P::NHAB, NHCD = P::NHCD, NH = P::NH;
@@ -249,7 +297,11 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_row(JKLaunch a) {
   constexpr int GS = P::GS, RPL = P::RPL, SL = P::SL, LCD = P::LCD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RowTables<LA, LB, LC, LD, VW> tb;
-  build_row_tables<LA, LB, LC, LD, VW>(tb);
+  // zero the staging memory once: padded slots (see below) then only ever
+  // hold finite values
+  for (int i = threadIdx.x; i < P::WARPS * P::WARP_BYTES / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(smem_raw)[i] = make_uint4(0u, 0u, 0u, 0u);
+  build_row_tables<LA, LB, LC, LD, VW>(tb);  // ends with __syncthreads
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / GS, gl = lane - g * GS;
   const bool in_group = g < P::NGW;
@@ -259,7 +311,6 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_row(JKLaunch a) {
   T* Rg = Gs + NAB * NCDP;    // R of the staged ket primitives [SL][NH]
   T* Eab = Rg + P::RSZ;       // bra E of the current bra primitive [3][EA]
   T* Eprod = Eab + P::EASZ;   // K_p E^ab_x E^ab_y E^ab_z [BT]
-  const unsigned gmask = (GS == 32) ? 0xffffffffu : (((1u << GS) - 1u) << (g * GS));
   const long long total = (long long)__ldg(a.prefix + a.nseg);
   const BasisView& bv = a.bv;
   const PrimPair<T>* __restrict__ pp = Prec<T>::pp(bv);
@@ -289,71 +340,105 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_row(JKLaunch a) {
     }
   }
 
+  // Every lane of a warp runs the same trip counts (the warp maxima), so the
+  // groups of a warp stay converged and every phase ends in a full-warp
+  // __syncwarp.  A group with less work (or none: lanes outside every group,
+  // or a group past the end of the work list) runs padded steps that write
+  // nothing and add zeros: its extra R slots are zeroed, and every slot holds
+  // finite values from the start.
+  constexpr unsigned FULL = 0xffffffffu;
   for (;;) {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(a.counter, (unsigned long long)P::NGW);
-    base = __shfl_sync(0xffffffffu, base, 0);
+    int stop = 0;
+    if (lane == 0) {
+      base = atomicAdd(a.counter, (unsigned long long)P::NGW);
+      stop = *(volatile const int*)a.abort_flag;
+    }
+    base = __shfl_sync(FULL, base, 0);
+    stop = __shfl_sync(FULL, stop, 0);
     if ((long long)base >= total) break;
-    if (*(volatile const int*)a.abort_flag) {
+    if (stop) {
       if (lane == 0) atomicCAS(a.status, 0, ADFT_ERR_ABORTED);
       break;
     }
     const long long qi = (long long)base + g;
-    if (!in_group || qi >= total) continue;
-    int bra, ket;
-    decode_quartet(a, qi, bra, ket);
-    const int off0 = __ldg(bv.pair_pp_off + bra), n0 = __ldg(bv.pair_pp_n + bra);
-    const int off1 = __ldg(bv.pair_pp_off + ket), n1 = __ldg(bv.pair_pp_n + ket);
-    const T AB[3] = {from_f64<T>(__ldg(bv.pair_AB + 3 * bra)), from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 1)),
-                     from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 2))};
-    const T CDx = from_f64<T>(__ldg(bv.pair_AB + 3 * ket)), CDy = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 1)),
-            CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
-    for (int x = gl; x < NAB * NCDP; x += GS) Gs[x] = T(0);
+    const bool valid = in_group && qi < total;
+    int bra = 0, ket = 0, off0 = 0, n0 = 0, off1 = 0, n1 = 0;
+    T AB[3] = {T(0), T(0), T(0)};
+    T CDx = T(0), CDy = T(0), CDz = T(0);
+    if (valid) {
+      decode_quartet(a, qi, bra, ket);
+      off0 = __ldg(bv.pair_pp_off + bra);
+      n0 = __ldg(bv.pair_pp_n + bra);
+      off1 = __ldg(bv.pair_pp_off + ket);
+      n1 = __ldg(bv.pair_pp_n + ket);
+      AB[0] = from_f64<T>(__ldg(bv.pair_AB + 3 * bra));
+      AB[1] = from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 1));
+      AB[2] = from_f64<T>(__ldg(bv.pair_AB + 3 * bra + 2));
+      CDx = from_f64<T>(__ldg(bv.pair_AB + 3 * ket));
+      CDy = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 1));
+      CDz = from_f64<T>(__ldg(bv.pair_AB + 3 * ket + 2));
+      for (int x = gl; x < NAB * NCDP; x += GS) Gs[x] = T(0);
+    }
+    const int n0max = __reduce_max_sync(FULL, n0);
     // all kept ket primitives in one batch: their e2 is built once and kept
     const bool keep_e2 = n1 <= SL;
     bool have_e2 = false;
 
     int n1e = n1;
-    for (int ip = 0; ip < n0; ++ip) {
-      n1e = shrink_kept(qa + off1, __ldg(qa + off0 + ip), eps, n1e);  // same in every lane
-      if (n1e == 0) break;
-      if (gl == 0) { cpq += n1e; ++cbp; }
-      const PrimPair<T> bp = pp[off0 + ip];
-      const T o2p = __ldg(o2pa + off0 + ip);
-      for (int d = gl; d < 3; d += GS) {  // groups may have fewer than 3 lanes
-        const T PA = d == 0 ? bp.PAx : d == 1 ? bp.PAy : bp.PAz;
-        const T ABd = d == 0 ? AB[0] : d == 1 ? AB[1] : AB[2];  // (no dynamic register index)
-        hermite_E<T, LA, LB>(PA, PA + ABd, o2p, Eab + d * EA);
+    for (int ip = 0; ip < n0max; ++ip) {
+      n1e = ip < n0 ? shrink_kept(qa + off1, __ldg(qa + off0 + ip), eps, n1e) : 0;  // same in a group
+      if (__all_sync(FULL, n1e == 0)) break;
+      const bool act = n1e > 0;  // this group evaluates bra primitive ip
+      if (gl == 0 && act) { cpq += n1e; ++cbp; }
+      PrimPair<T> bp = {};
+      T o2p = T(0);
+      if (act) {
+        bp = pp[off0 + ip];
+        o2p = __ldg(o2pa + off0 + ip);
+        for (int d = gl; d < 3; d += GS) {  // groups may have fewer than 3 lanes
+          const T PA = d == 0 ? bp.PAx : d == 1 ? bp.PAy : bp.PAz;
+          const T ABd = d == 0 ? AB[0] : d == 1 ? AB[1] : AB[2];  // (no dynamic register index)
+          hermite_E<T, LA, LB>(PA, PA + ABd, o2p, Eab + d * EA);
+        }
       }
       T W[RPL][NCD];
 #pragma unroll
       for (int i = 0; i < RPL; ++i)
 #pragma unroll
         for (int c = 0; c < NCD; ++c) W[i][c] = T(0);
-      __syncwarp(gmask);
-      for (int k = gl; k < BT; k += GS) {
-        const unsigned c = tb.bcode[k];
-        Eprod[k] = bp.K * Eab[c & 255u] * Eab[EA + ((c >> 8) & 255u)] * Eab[2 * EA + (c >> 16)];
-      }
-      for (int q0 = 0; q0 < n1e; q0 += SL) {
-        const int nv = min(SL, n1e - q0);
-        const bool build = !have_e2;
-        if (gl < nv) {
-          const int iq = off1 + q0 + gl;
-          const PrimPair<T> kq = pp[iq];
-          const T o2q = __ldg(o2pa + iq);
-          if (build) {
-            T* Ec = WE + gl * 3 * EC;
-            hermite_E<T, LC, LD>(kq.PAx, kq.PAx + CDx, o2q, Ec);
-            hermite_E<T, LC, LD>(kq.PAy, kq.PAy + CDy, o2q, Ec + EC);
-            hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CDz, o2q, Ec + 2 * EC);
-          }
-          const T r = Prec<T>::rsq(bp.p + kq.p);
-          const T alpha = bp.p * kq.p * r * r;
-          const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
-          prim_R_scaled<T, P::L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, pref, bv, Rg + gl * NH);
+      __syncwarp();
+      if (act)
+        for (int k = gl; k < BT; k += GS) {
+          const unsigned c = tb.bcode[k];
+          Eprod[k] = bp.K * Eab[c & 255u] * Eab[EA + ((c >> 8) & 255u)] * Eab[2 * EA + (c >> 16)];
         }
-        __syncwarp(gmask);
+      const int nbmax = __reduce_max_sync(FULL, n1e);
+      for (int q0 = 0; q0 < nbmax; q0 += SL) {
+        const int nvmax = min(SL, nbmax - q0);          // warp-uniform slot count
+        const int nv = max(0, min(SL, n1e - q0));       // this group's slots
+        const bool build = act && !have_e2;
+        if (in_group && gl < nvmax) {
+          T* Rs = Rg + gl * NH;
+          if (gl < nv) {
+            const int iq = off1 + q0 + gl;
+            const PrimPair<T> kq = pp[iq];
+            const T o2q = __ldg(o2pa + iq);
+            if (build) {
+              T* Ec = WE + gl * 3 * EC;
+              hermite_E<T, LC, LD>(kq.PAx, kq.PAx + CDx, o2q, Ec);
+              hermite_E<T, LC, LD>(kq.PAy, kq.PAy + CDy, o2q, Ec + EC);
+              hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CDz, o2q, Ec + 2 * EC);
+            }
+            const T r = Prec<T>::rsq(bp.p + kq.p);
+            const T alpha = bp.p * kq.p * r * r;
+            const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+            prim_R_scaled<T, P::L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, pref, bv, Rs);
+          } else {
+            for (int x = 0; x < NH; ++x) Rs[x] = T(0);  // padded slot: adds zero
+          }
+        }
+        __syncwarp();
         if (build) {
           for (int e = gl; e < nv * KSIZE; e += GS) {
             const int s = e / KSIZE;
@@ -367,10 +452,10 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_row(JKLaunch a) {
             e2g[e] = val;
           }
           have_e2 = keep_e2;
-          __syncwarp(gmask);
         }
+        __syncwarp();
         // ket transform, term-major (see the top of the file)
-        for (int s = 0; s < nv; ++s) {
+        for (int s = 0; s < nvmax; ++s) {
           const T* Rs = Rg + s * NH;
           const T* es = e2g + s * KSIZE;
           static_for<NHCD>([&](auto jj) {
@@ -396,38 +481,41 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_row(JKLaunch a) {
             });
           });
         }
-        __syncwarp(gmask);
+        __syncwarp();
       }
       // W rows to shared memory (padding columns zero), then the bra
       // transform: lane unit (ab, VW ket components)
+      if (act) {
 #pragma unroll
-      for (int i = 0; i < RPL; ++i) {
-        const int h = gl + GS * i;
-        if (h < NHAB) {
-          static_for<NCDP / VW>([&](auto cc) {
-            constexpr int c0 = decltype(cc)::value * VW;
-            *reinterpret_cast<V*>(WE + h * NCDP + c0) = RV::template pack<c0, NCD>(W[i]);
-          });
+        for (int i = 0; i < RPL; ++i) {
+          const int h = gl + GS * i;
+          if (h < NHAB) {
+            static_for<NCDP / VW>([&](auto cc) {
+              constexpr int c0 = decltype(cc)::value * VW;
+              *reinterpret_cast<V*>(WE + h * NCDP + c0) = RV::template pack<c0, NCD>(W[i]);
+            });
+          }
         }
       }
-      __syncwarp(gmask);
-      constexpr int NV = NCDP / VW;
-      for (int u = gl; u < NAB * NV; u += GS) {
-        const int ab = u / NV, c0 = (u - ab * NV) * VW;
-        V acc = RV::zero();
-        const int k1 = tb.first[ab + 1];
-        for (int k = tb.first[ab]; k < k1; ++k)
-          RV::fma(acc, Eprod[k], *reinterpret_cast<const V*>(WE + tb.h[k] * NCDP + c0));
-        V* gp = reinterpret_cast<V*>(Gs + ab * NCDP + c0);
-        V gv = *gp;
-        RV::add(gv, acc);
-        *gp = gv;
+      __syncwarp();
+      if (act) {
+        constexpr int NV = NCDP / VW;
+        for (int u = gl; u < NAB * NV; u += GS) {
+          const int ab = u / NV, c0 = (u - ab * NV) * VW;
+          V acc = RV::zero();
+          const int k1 = tb.first[ab + 1];
+          for (int k = tb.first[ab]; k < k1; ++k)
+            RV::fma(acc, Eprod[k], *reinterpret_cast<const V*>(WE + tb.h[k] * NCDP + c0));
+          V* gp = reinterpret_cast<V*>(Gs + ab * NCDP + c0);
+          V gv = *gp;
+          RV::add(gv, acc);
+          *gp = gv;
+        }
       }
-      __syncwarp(gmask);
+      __syncwarp();
     }
-    __syncwarp(gmask);  // the digestion reads the whole group's block
-    digest_coop<T, LA, LB, LC, LD, NCDP>(a, bra, ket, gl, GS, Gs);
-    __syncwarp(gmask);
+    if (valid) digest_coop<T, LA, LB, LC, LD, NCDP>(a, bra, ket, gl, GS, Gs);
+    __syncwarp();
   }
   flush_work(a.work, cpq, cbp);
 }

@@ -74,7 +74,7 @@ def test_autotune_keeps_results():
     J0, K0 = adft.adft_jk_build(b, D, thresh=opt["thresh"], precision="mixed")
     tab = adft.adft_autotune(b, D, thresh=opt["thresh"], precision="mixed")
     blocks, variant = tab % adft.TUNE_VARIANT_STRIDE, tab // adft.TUNE_VARIANT_STRIDE
-    assert tab.shape == (2, 55) and np.all((blocks >= 1) & (blocks <= 8)) and np.all((variant >= 0) & (variant <= 2))
+    assert tab.shape == (2, 55) and np.all((blocks >= 1) & (blocks <= 8)) and np.all((variant >= 0) & (variant <= 3))
     J1, K1 = adft.adft_jk_build(b, D, thresh=opt["thresh"], precision="mixed")
     assert torch.max(torch.abs(J1 - J0)).item() <= 1e-12 * torch.max(torch.abs(J0)).item()
     assert torch.max(torch.abs(K1 - K0)).item() <= 1e-12 * torch.max(torch.abs(K0)).item()

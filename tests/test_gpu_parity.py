@@ -80,9 +80,11 @@ def test_mixed_precision_energy(name, split):
 def _variant_pairs(b, variant):
     """Class pairs X(X+1)/2 + Y of each band (0 FP64, 1 FP32) with a kernel
     variant `variant`: adft_set_tuning rejects a variant past a pair's count.
-    Variant 1 is the warp or cooperative kernel of the pairs served by both
-    (the row-blocked kernel of the pairs served by the cooperative one only),
-    variant 2 the row-blocked kernel of the pairs served by all three."""
+    The d-class pairs list their kernels as: the warp and the cooperative
+    kernel (where both serve the pair; the cooperative one alone otherwise),
+    then the row-blocked kernel with its busiest shape and with its
+    occupancy-aware shape (where each plan fits and the two differ).  So
+    variants 1-3 together cover every kernel but the default one."""
     found = {0: [], 1: []}
     for band in (0, 1):
         for cp in range(55):
@@ -96,18 +98,22 @@ def _variant_pairs(b, variant):
     return found
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_alternative_kernel_variant_parity(variant, precision):
     mol, opt, D = _case("small")
     Jr, Kr, Er = _oracle_jk("small", True, mol, D, opt["thresh"])
     b = adft.Basis.from_molecule(mol)
     pairs = _variant_pairs(b, variant)
-    # (dp|pp), (dp|ds), (dp|dp) have a second and a third kernel in FP32;
-    # every d-class pair up to (dd|dp) has a second one
-    assert {12, 13, 14} <= set(pairs[1]), pairs
+    # (dp|pp), (dp|ds), (dp|dp) have at least three kernels in both bands,
+    # every d-class pair up to (dd|dp) at least two, and (dp|pp), (dp|dp)
+    # four (both row-kernel shapes)
+    if variant <= 2:
+        assert {12, 13, 14} <= set(pairs[0]) and {12, 13, 14} <= set(pairs[1]), pairs
     if variant == 1:
-        assert {12, 13, 14, 19} <= set(pairs[0]) and {19} <= set(pairs[1]), pairs
+        assert {19} <= set(pairs[0]) and {19} <= set(pairs[1]), pairs
+    if variant == 3:
+        assert {12, 14} <= set(pairs[0]) and {12, 14} <= set(pairs[1]), pairs
     tab = np.full((2, 55), 2, dtype=np.int32)
     for band in (0, 1):
         tab[band, pairs[band]] += variant * adft.TUNE_VARIANT_STRIDE
