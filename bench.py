@@ -557,13 +557,21 @@ def main():
             adft.adft_set_tuning(basis, tab)
 
     # ---- roofline of the dominant kernel group (the ALU-bound ERI kernels of a band)
+    # traffic: DRAM bytes (read + write) of the band's class-pair launches in one
+    # build, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
+    # over every launch of one mixed c240 build at split 3e-3, the kernels of
+    # this version); null for other workloads and splits
+    traffic = {}
+    if args.workload == "c240" and prec == "mixed" and split == 3e-3:
+        traffic = {"eri_fp32": 1.507378e9 + 0.234573e9, "eri_fp64": 4.169497e9 + 56.850255e9}
     groups = {"eri_fp32": (ph["eri_fp32_ms"], float(cls["flops"][1].sum()), peaks["fp32"]["tflops"], "FP32"),
               "eri_fp64": (ph["eri_fp64_ms"], float(cls["flops"][0].sum()), peaks["fp64"]["tflops"], "FP64")}
     dom = max(groups, key=lambda k: groups[k][0])
     gms, gfl, gpk, gkind = groups[dom]
     ach = gfl / (gms / 1e3) / 1e12 if gms > 0 else 0.0
     roof = {"bound": "alu", "kernel": f"{dom} (all class-pair launches of the band)", "achieved": ach,
-            "peak": gpk, "unit": "TFLOP/s", "frac": ach / gpk if gpk else None, "traffic": None,
+            "peak": gpk, "unit": "TFLOP/s", "frac": ach / gpk if gpk else None, "traffic": traffic.get(dom),
+            "traffic_unit": "bytes per build (all launches of the band)",
             "peak_kind": f"measured in this run: adft_alu_peak ({gkind} FMA chains on every SM)",
             "flops_model": "class_flops per evaluated primitive quartet, bra primitive and quartet",
             "other": {k: {"ms": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0.0,
