@@ -108,6 +108,14 @@ typedef struct {
                       so one sum all-reduce of J and K (or E, or the gradient) is
                       the only exchange.  Single-molecule calls only (a batch is
                       sharded by molecules). */
+  double omega;    /* range separation: 0 = the Coulomb operator 1/r12; > 0 = the
+                      long-range operator erf(omega r12)/r12 of range-separated
+                      hybrids (the omegaB97X functional of Sec. 4.1) in every ERI of J
+                      and K (adft_jk_build, adft_jk_energy, adft_autotune).  Quartets
+                      are still screened with the Coulomb bounds Q, which bound the
+                      attenuated integrals too.  Must be finite and >= 0
+                      (ADFT_ERR_ARG); adft_jk_grad and the batched calls return
+                      ADFT_ERR_UNSUPPORTED for omega > 0. */
 } adft_opts;
 
 /* Per-call statistics of the last J/K build (host copies).  After a build

@@ -12,7 +12,9 @@ Every function cites what it follows:
 * the ERI: the integral in the ERI paragraph of Sec. 1.2.2;
 * screening: the Cauchy-Schwarz bound of the mixed-precision bullet of
   Sec. 1.2.2 (skip a shell quartet iff Q_ab Q_cd < thresh);
-* energy E = 1/2 tr(DJ) - 1/4 tr(DK) and its nuclear gradient at fixed D.
+* energy E = 1/2 tr(DJ) - 1/4 tr(DK) and its nuclear gradient at fixed D;
+* optionally the long-range ERI over erf(omega r)/r, the operator of the
+  range-separated hybrid (omegaB97X) of the comparative benchmark, Sec. 4.1.
 """
 from __future__ import annotations
 
@@ -48,10 +50,14 @@ def lib():
         basis = [dp, ctypes.c_int, ip, ip, ip, ip, dp, dp]
         L.orc_boys.argtypes = [ctypes.c_int, ctypes.c_double, dp]
         L.orc_prim_block.argtypes = [ctypes.c_int] * 4 + [dp, ctypes.c_double] * 4 + [ctypes.c_double, dp]
+        L.orc_prim_block_omega.argtypes = [ctypes.c_int] * 4 + [dp, ctypes.c_double] * 4 + [ctypes.c_double] * 2 + \
+            [dp]
         L.orc_shell_quartet.argtypes = basis + [ctypes.c_int] * 4 + [dp]
         L.orc_schwarz.argtypes = basis + [dp, ctypes.c_int]
         L.orc_jk.argtypes = basis + [dp, ctypes.c_double, dp, dp, dp, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_long)]
+        L.orc_jk_omega.argtypes = basis + [dp, ctypes.c_double, dp, dp, dp, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_long), ctypes.c_double]
         L.orc_jk_range.argtypes = basis + [dp, ctypes.c_double, dp, dp, dp, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_long), ctypes.c_long, ctypes.c_long]
         L.orc_jk_blocks.argtypes = basis + [dp, ctypes.c_double, dp, ctypes.c_int, ip, dp, dp, ctypes.c_int]
@@ -87,14 +93,18 @@ def boys(mmax: int, T: float) -> np.ndarray:
     return out
 
 
-def prim_block(ls, centres, exps, scale=1.0) -> np.ndarray:
-    """Unnormalised primitive Cartesian [ab|cd] for total powers ls=(la,lb,lc,ld)."""
+def prim_block(ls, centres, exps, scale=1.0, omega=0.0) -> np.ndarray:
+    """Unnormalised primitive Cartesian [ab|cd] for total powers ls=(la,lb,lc,ld);
+    with omega > 0 over the long-range operator erf(omega r)/r."""
     out = np.zeros([ncart(l) for l in ls])
     cs = [np.ascontiguousarray(c, dtype=np.float64) for c in centres]
     args = []
     for c, e in zip(cs, exps):
         args += [_p(c), float(e)]
-    lib().orc_prim_block(*[int(l) for l in ls], *args, float(scale), _p(out))
+    if omega > 0.0:
+        lib().orc_prim_block_omega(*[int(l) for l in ls], *args, float(scale), float(omega), _p(out))
+    else:
+        lib().orc_prim_block(*[int(l) for l in ls], *args, float(scale), _p(out))
     return out
 
 
@@ -243,8 +253,10 @@ def schwarz_full(mol, Q=None) -> np.ndarray:
     return M
 
 
-def jk(mol, D, thresh, Q=None, nthreads=None, return_kept=False):
-    """J, K in the basis of D (spherical iff mol.spherical), scatter mode."""
+def jk(mol, D, thresh, Q=None, nthreads=None, return_kept=False, omega=0.0):
+    """J, K in the basis of D (spherical iff mol.spherical), scatter mode.
+    omega > 0: J and K of the long-range operator erf(omega r)/r (the
+    quartets screened with the Coulomb bounds Q)."""
     B = _Basis(mol)
     if Q is None:
         Q = schwarz(mol, nthreads)
@@ -252,8 +264,12 @@ def jk(mol, D, thresh, Q=None, nthreads=None, return_kept=False):
     J = np.zeros((B.nc, B.nc))
     K = np.zeros((B.nc, B.nc))
     kept = ctypes.c_long(0)
-    lib().orc_jk(*B.args(), _p(np.ascontiguousarray(Q)), float(thresh), _p(Dc), _p(J), _p(K),
-                 _nthreads(nthreads), ctypes.byref(kept))
+    if omega > 0.0:
+        lib().orc_jk_omega(*B.args(), _p(np.ascontiguousarray(Q)), float(thresh), _p(Dc), _p(J), _p(K),
+                           _nthreads(nthreads), ctypes.byref(kept), float(omega))
+    else:
+        lib().orc_jk(*B.args(), _p(np.ascontiguousarray(Q)), float(thresh), _p(Dc), _p(J), _p(K),
+                     _nthreads(nthreads), ctypes.byref(kept))
     J, K = _from_cart(mol, J), _from_cart(mol, K)
     return (J, K, kept.value) if return_kept else (J, K)
 

@@ -18,6 +18,8 @@
  *   Q_ab * Q_cd < thresh, Q_ab = sqrt(max_{mu in a, nu in b} |(mu nu|mu nu)|)
  *                                      (Sec. 1.2.2, mixed-precision bullet)
  *   dE/dR_A with E = 1/2 tr(DJ) - 1/4 tr(DK) at fixed D.
+ *   Optionally the long-range (erf-attenuated) operator erf(omega r)/r in
+ *   place of 1/r in the ERIs and J, K (range-separated hybrids; omega > 0).
  *
  * Primitive integrals follow the McMurchie-Davidson scheme as written in
  * Helgaker, Jorgensen and Olsen, "Molecular Electronic-Structure Theory",
@@ -182,13 +184,22 @@ static int cart_index(int l, int ax, int ay) {
    [ab|cd] = 2 pi^(5/2) / (p q sqrt(p+q)) sum_{tuv} E^ab_{tuv}
              sum_{tau nu phi} (-1)^(tau+nu+phi) E^cd_{tau nu phi} R_{t+tau,u+nu,v+phi} */
 
-void orc_prim_block(int la, int lb, int lc, int ld,
-                    const double *A, double a, const double *B, double b,
-                    const double *C, double c, const double *D, double d,
-                    double scale, double *out) {
+/* With omega > 0 the operator is erf(omega r12)/r12.  Its Fourier transform
+   is that of 1/r12 times exp(-k^2/(4 omega^2)), and the two charge
+   distributions contribute exp(-k^2/(4p)) exp(-k^2/(4q)) = exp(-k^2/(4 alpha)),
+   so the integral is the Coulomb one with 1/alpha replaced by
+   1/alpha + 1/omega^2: alpha_w = alpha w / (alpha + w), w = omega^2, in the
+   Boys argument and in the (-2 alpha)^n of the Hermite integrals, and the
+   prefactor 2 pi^(5/2) / (p q sqrt(p+q)) times sqrt(alpha_w / alpha). */
+static void prim_block_w(int la, int lb, int lc, int ld,
+                         const double *A, double a, const double *B, double b,
+                         const double *C, double c, const double *D, double d,
+                         double scale, double omega, double *out) {
   if (la < 0 || lb < 0 || lc < 0 || ld < 0) return;
   const int L = la + lb + lc + ld;
-  const double p = a + b, q = c + d, alpha = p * q / (p + q);
+  const double p = a + b, q = c + d, alpha_c = p * q / (p + q);
+  const double w = omega * omega;
+  const double alpha = omega > 0.0 ? alpha_c * w / (alpha_c + w) : alpha_c;
   double P[3], Q[3];
   for (int k = 0; k < 3; ++k) {
     P[k] = (a * A[k] + b * B[k]) / p;
@@ -204,7 +215,7 @@ void orc_prim_block(int la, int lb, int lc, int ld,
   }
   double R[(L + 1) * (L + 1) * (L + 1)];
   hermite_r(L, alpha, P[0] - Q[0], P[1] - Q[1], P[2] - Q[2], R);
-  const double pref = scale * 2.0 * pow((double)ORC_PI, 2.5) / (p * q * sqrt(p + q));
+  const double pref = scale * 2.0 * pow((double)ORC_PI, 2.5) / (p * q * sqrt(p + q)) * sqrt(alpha / alpha_c);
 
   int pa[3 * ORC_NC(ORC_LMAX)], pb[3 * ORC_NC(ORC_LMAX)], pc[3 * ORC_NC(ORC_LMAX)], pd[3 * ORC_NC(ORC_LMAX)];
   cart_list(la, pa); cart_list(lb, pb); cart_list(lc, pc); cart_list(ld, pd);
@@ -236,6 +247,20 @@ void orc_prim_block(int la, int lb, int lc, int ld,
 #undef ECD
 }
 
+void orc_prim_block(int la, int lb, int lc, int ld,
+                    const double *A, double a, const double *B, double b,
+                    const double *C, double c, const double *D, double d,
+                    double scale, double *out) {
+  prim_block_w(la, lb, lc, ld, A, a, B, b, C, c, D, d, scale, 0.0, out);
+}
+
+void orc_prim_block_omega(int la, int lb, int lc, int ld,
+                          const double *A, double a, const double *B, double b,
+                          const double *C, double c, const double *D, double d,
+                          double scale, double omega, double *out) {
+  prim_block_w(la, lb, lc, ld, A, a, B, b, C, c, D, d, scale, omega, out);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Basis description passed by the wrapper */
 
@@ -244,6 +269,7 @@ typedef struct {
   int nshell;
   const int *atom, *l, *nprim, *ptr;      /* per shell */
   const double *exps, *coefs;             /* primitives */
+  double omega;                           /* > 0: erf(omega r)/r operator */
 } orc_basis;
 
 static double dfact(int n) {
@@ -273,7 +299,7 @@ static void shell_quartet(const orc_basis *bs, int sa, int sb, int sc, int sd, d
                            bs->coefs[bs->ptr[sb] + j] * prim_norm(b, lb) *
                            bs->coefs[bs->ptr[sc] + k] * prim_norm(c, lc) *
                            bs->coefs[bs->ptr[sd] + m] * prim_norm(d, ld);
-          orc_prim_block(la, lb, lc, ld, A, a, B, b, C, c, D, d, s, out);
+          prim_block_w(la, lb, lc, ld, A, a, B, b, C, c, D, d, s, bs->omega, out);
         }
 }
 
@@ -379,13 +405,24 @@ static void scatter_jk(const int *sh, const int *off, const int *nsz, const doub
 
 static void jk_range(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
                      const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
-                     const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi);
+                     const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi,
+                     double omega);
 
 void orc_jk(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
             const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
             const double *D, double *J, double *K, int nthreads, long *nkept) {
   jk_range(xyz, nshell, atom, l, nprim, ptr, exps, coefs, Q, thresh, D, J, K, nthreads, nkept, 0,
-           (long)nshell * (nshell + 1) / 2);
+           (long)nshell * (nshell + 1) / 2, 0.0);
+}
+
+/* The same with the long-range operator erf(omega r)/r (omega > 0); the
+   quartets are screened with the Coulomb bounds Q, which bound the
+   attenuated integrals too. */
+void orc_jk_omega(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
+                  const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
+                  const double *D, double *J, double *K, int nthreads, long *nkept, double omega) {
+  jk_range(xyz, nshell, atom, l, nprim, ptr, exps, coefs, Q, thresh, D, J, K, nthreads, nkept, 0,
+           (long)nshell * (nshell + 1) / 2, omega);
 }
 
 /* The same sum restricted to bra pairs ab in [ab_lo, ab_hi) (each with all
@@ -393,13 +430,14 @@ void orc_jk(const double *xyz, int nshell, const int *atom, const int *l, const 
 void orc_jk_range(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
                   const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
                   const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi) {
-  jk_range(xyz, nshell, atom, l, nprim, ptr, exps, coefs, Q, thresh, D, J, K, nthreads, nkept, ab_lo, ab_hi);
+  jk_range(xyz, nshell, atom, l, nprim, ptr, exps, coefs, Q, thresh, D, J, K, nthreads, nkept, ab_lo, ab_hi, 0.0);
 }
 
 static void jk_range(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
                      const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
-                     const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi) {
-  orc_basis bs = {xyz, nshell, atom, l, nprim, ptr, exps, coefs};
+                     const double *D, double *J, double *K, int nthreads, long *nkept, long ab_lo, long ab_hi,
+                     double omega) {
+  orc_basis bs = {xyz, nshell, atom, l, nprim, ptr, exps, coefs, omega};
   int *off = (int *)malloc(sizeof(int) * (nshell + 1));
   shell_offsets(&bs, off);
   const int nc = off[nshell];

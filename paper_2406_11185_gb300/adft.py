@@ -52,7 +52,8 @@ class adft_shell(ctypes.Structure):
 
 class adft_opts(ctypes.Structure):
     _fields_ = [("thresh", ctypes.c_double), ("split", ctypes.c_double), ("precision", ctypes.c_int),
-                ("check", ctypes.c_int), ("stream", ctypes.c_void_p), ("pair_mask", ctypes.c_void_p)]
+                ("check", ctypes.c_int), ("stream", ctypes.c_void_p), ("pair_mask", ctypes.c_void_p),
+                ("omega", ctypes.c_double)]
 
 
 class adft_stats(ctypes.Structure):
@@ -133,12 +134,14 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def make_opts(thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None, pair_mask=None) -> adft_opts:
+def make_opts(thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None, pair_mask=None,
+              omega=0.0) -> adft_opts:
     """adft_opts; pair_mask: None or [2, 55] of 0/1 (band, class pair) owned by
-    this call (the array is kept alive by the returned structure)."""
+    this call (the array is kept alive by the returned structure); omega > 0:
+    the long-range operator erf(omega r)/r."""
     prec = {"fp64": ADFT_PREC_FP64, "mixed": ADFT_PREC_MIXED}[precision] if isinstance(precision, str) \
         else int(precision)
-    o = adft_opts(float(thresh), float(split), prec, 1 if check else 0, _stream_ptr(stream), None)
+    o = adft_opts(float(thresh), float(split), prec, 1 if check else 0, _stream_ptr(stream), None, float(omega))
     if pair_mask is not None:
         m = np.ascontiguousarray(np.asarray(pair_mask, dtype=np.uint8).reshape(-1))
         if m.size != 2 * NCP:
@@ -207,25 +210,27 @@ def _check_matrix(D, n):
 
 
 def adft_jk_build(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None, out=None,
-                  pair_mask=None):
+                  pair_mask=None, omega=0.0):
     """J, K (torch CUDA float64) of Eq. 1 for density D (partial sums over the
-    class pairs of pair_mask, if given)."""
+    class pairs of pair_mask, if given); omega > 0: J and K of the long-range
+    operator erf(omega r)/r."""
     import torch
     _check_matrix(D, basis.nbf)
     J, K = out if out is not None else (torch.empty_like(D), torch.empty_like(D))
-    o = make_opts(thresh, split, precision, check, stream, pair_mask)
+    o = make_opts(thresh, split, precision, check, stream, pair_mask, omega)
     _check(load().adft_jk_build(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
                                 ctypes.c_void_p(J.data_ptr()), ctypes.c_void_p(K.data_ptr())), "adft_jk_build")
     return J, K
 
 
 def adft_jk_energy(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None,
-                   on_device=False, pair_mask=None):
+                   on_device=False, pair_mask=None, omega=0.0):
     """E_JK = 1/2 tr(DJ) - 1/4 tr(DK); a float, or a 1-element CUDA tensor
-    (a partial sum over the class pairs of pair_mask, if given)."""
+    (a partial sum over the class pairs of pair_mask, if given); omega > 0:
+    with J and K of erf(omega r)/r."""
     import torch
     _check_matrix(D, basis.nbf)
-    o = make_opts(thresh, split, precision, check, stream, pair_mask)
+    o = make_opts(thresh, split, precision, check, stream, pair_mask, omega)
     if on_device:
         E = torch.empty(1, dtype=torch.float64, device=D.device)
         _check(load().adft_jk_energy(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
@@ -238,13 +243,14 @@ def adft_jk_energy(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", 
 
 
 def adft_jk_grad(basis: Basis, D, thresh=1e-12, split=1e-5, precision="fp64", check=True, stream=None,
-                 pair_mask=None):
+                 pair_mask=None, omega=0.0):
     """dE_JK/dR [natom, 3] (torch CUDA float64) at fixed D (a partial sum over
-    the class pairs of pair_mask, if given)."""
+    the class pairs of pair_mask, if given).  omega > 0 is not supported
+    (ADFT_ERR_UNSUPPORTED)."""
     import torch
     _check_matrix(D, basis.nbf)
     g = torch.empty((basis.natom, 3), dtype=torch.float64, device=D.device)
-    o = make_opts(thresh, split, precision, check, stream, pair_mask)
+    o = make_opts(thresh, split, precision, check, stream, pair_mask, omega)
     _check(load().adft_jk_grad(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o),
                                ctypes.c_void_p(g.data_ptr())), "adft_jk_grad")
     return g
@@ -360,7 +366,7 @@ NCP = 55  # class pairs up to f shells
 
 
 def adft_autotune(basis: Basis, D, thresh=1e-12, split=1e-5, precision="mixed", stream=None,
-                  return_times=False):
+                  return_times=False, omega=0.0):
     """Run the launch-shape autotuner on density D; returns the [2, 55] table
     (FP64 band, FP32 band) now installed in the handle, each entry
     blocks_per_SM + TUNE_VARIANT_STRIDE * kernel_variant (and the best kernel
@@ -368,7 +374,7 @@ def adft_autotune(basis: Basis, D, thresh=1e-12, split=1e-5, precision="mixed", 
     _check_matrix(D, basis.nbf)
     tab = (ctypes.c_int * (2 * NCP))()
     ms = (ctypes.c_double * (2 * NCP))()
-    o = make_opts(thresh, split, precision, False, stream)
+    o = make_opts(thresh, split, precision, False, stream, omega=omega)
     _check(load().adft_autotune(basis.handle, ctypes.c_void_p(D.data_ptr()), ctypes.byref(o), tab, ms),
            "adft_autotune")
     t = np.array(tab[:], dtype=np.int32).reshape(2, NCP)

@@ -725,6 +725,7 @@ static JKLaunch base_launch(adft_basis* b) {
   L.status = w.status;
   L.prim_eps = 0.0;
   L.work = nullptr;
+  L.omega2 = 0.0;
   return L;
 }
 
@@ -748,6 +749,7 @@ static int for_each_class_pair(adft_basis* b, const adft_opts* o, JKLaunch L, cu
         L.ket_start = (band ? w.kst32 : w.kst64) + b->cnt_off[cp];
         L.counter = w.counters + 2 * NCP * pass + 2 * cp + band;
         L.prim_eps = PRIM_QUARTET_FRAC * o->thresh;
+        L.omega2 = o->omega * o->omega;
         L.work = w.work + 2 * (band * NCP + cp);
         const int grid = b->sms * b->tune_blocks[band][cp];
         cudaError_t e = fn(X, Y, L, band, grid, b->tune_variant[band][cp]);
@@ -841,6 +843,7 @@ static int check_opts(const adft_opts* o) {
     return ADFT_ERR_ARG;
   }
   if (o->check != 0 && o->check != 1) { set_error("check must be 0 or 1"); return ADFT_ERR_ARG; }
+  if (!(o->omega >= 0.0) || !isfinite(o->omega)) { set_error("omega must be finite and >= 0"); return ADFT_ERR_ARG; }
   return ADFT_OK;
 }
 
@@ -1292,6 +1295,7 @@ int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* o, double* gra
   int st = call_begin(b, D, o);
   if (st) return st;
   if (!grad) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  if (o->omega > 0.0) { set_error("adft_jk_grad: omega > 0 is not supported"); return ADFT_ERR_UNSUPPORTED; }
   cudaStream_t s = (cudaStream_t)o->stream;
   if ((st = prepare(b, D, o, s))) return st;
   if ((st = run_grad(b, o, s, grad, 0))) return st;
@@ -1454,6 +1458,7 @@ int adft_autotune(adft_basis* b, const double* D, const adft_opts* o, int* table
         L.ket_start = (band ? b->ws.kst32 : b->ws.kst64) + b->cnt_off[cp];
         L.counter = b->ws.counters + 2 * NCP + 2 * cp + band;
         L.prim_eps = PRIM_QUARTET_FRAC * o->thresh;
+        L.omega2 = o->omega * o->omega;
         KernelInfo ki{1, 1};
         ADFT_CUDA(launch_band(band, X, Y, L, 0, 0, s, &ki));
         float best = 1e30f;
@@ -1590,6 +1595,7 @@ int adft_batch_jk(adft_batch* bt, const double* D, const adft_opts* o, double* J
   if (st) return st;
   if (!J || !K) { set_error("NULL argument"); return ADFT_ERR_ARG; }
   if (o->pair_mask) { set_error("pair_mask is for single-molecule calls; shard a batch by molecules"); return ADFT_ERR_ARG; }
+  if (o->omega > 0.0) { set_error("adft_batch_jk: omega > 0 is not supported"); return ADFT_ERR_UNSUPPORTED; }
   cudaStream_t s = (cudaStream_t)o->stream;
   if (o->check || s == nullptr) {
     // direct launches (validation needs a synchronisation; the legacy
@@ -1634,6 +1640,7 @@ int adft_batch_last_timings(adft_batch* bt, double* ms) {
 
 int adft_batch_autotune(adft_batch* bt, const double* D, const adft_opts* o, int* table, double* ms) {
   if (!bt) { set_error("NULL batch"); return ADFT_ERR_ARG; }
+  if (o && o->omega > 0.0) { set_error("adft_batch_autotune: omega > 0 is not supported"); return ADFT_ERR_UNSUPPORTED; }
   if (bt->has_graph) {  // the captured graph holds the old launch shapes
     cudaGraphExecDestroy(bt->exec); cudaGraphDestroy(bt->graph);
     bt->exec = nullptr; bt->graph = nullptr; bt->has_graph = false;

@@ -76,6 +76,21 @@ template <> struct Prec<float> {
   static constexpr int BUDGET = 640;
 };
 
+// Long-range operator erf(omega r)/r (range-separated hybrids, the omegaB97X
+// functional of Sec. 4.1).  Its Fourier transform is that of 1/r times
+// exp(-k^2 / (4 w2)), w2 = omega^2, so a primitive quartet's integral is the
+// Coulomb one with 1/alpha -> 1/alpha + 1/w2: alpha -> alpha w2 / (alpha + w2)
+// in the Boys argument and in the Hermite recursion, and the prefactor times
+// sqrt(w2 / (alpha + w2)).  w2 = 0 leaves both untouched (the 1/r operator).
+template <typename T>
+__device__ __forceinline__ void attenuate(T w2, T& alpha, T& pref) {
+  if (w2 > T(0)) {
+    const T s = w2 / (alpha + w2);
+    alpha *= s;
+    pref *= sqrt(s);
+  }
+}
+
 // Primitive-quartet screening inside a kept shell quartet: the primitive
 // pairs of a pair are stored by descending bound Q_p, so the ket primitives q
 // kept for bra primitive p (Q_p Q_q >= eps) are a prefix of the ket's list,
@@ -293,7 +308,7 @@ __device__ __forceinline__ void static_for(F&& f) {
 // primitives evaluated.
 template <typename T, int LA, int LB, int LC, int LD, int C0, int NK>
 __device__ __forceinline__ void quartet_block_range(const BasisView& bv, int bra, int ket, T* G, T eps, int& npq,
-                                                    int& nbp) {
+                                                    int& nbp, T w2) {
   constexpr int NB = ncart(LB), ND = ncart(LD);
   constexpr int NAB = ncart(LA) * NB, NCD = ncart(LC) * ND;
   constexpr int LAB = LA + LB, LCD = LC + LD, L = LAB + LCD;
@@ -337,10 +352,11 @@ __device__ __forceinline__ void quartet_block_range(const BasisView& bv, int bra
       hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CDz, o2q, Ecd[2]);
       // 1/(p+q) = r^2, alpha = p q r^2, 2 pi^(5/2) K_q / (p q sqrt(p+q)) = 4 (2 pi^(5/2)) K_q r o2p o2q
       const T r = Prec<T>::rsq(bp.p + kq.p);
-      const T alpha = bp.p * kq.p * r * r;
+      T alpha = bp.p * kq.p * r * r;
+      T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+      attenuate(w2, alpha, pref);
       T R[nherm(L)];
       prim_R<T, L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
-      const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
       // ket transform W[tuv][cd] += sum_{tau nu phi} (+-) E^cd R_{t+tau, u+nu, v+phi}
       static_for<NK>([&](auto kk) {
         constexpr int k = decltype(kk)::value, kc = C0 + k;
@@ -584,7 +600,8 @@ using GenSizes = RtSizes<GEN_E, GEN_NH, GEN_BUDGET>;
 template <typename T, typename S = GenSizes>
 __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView& bv, int bra, int ket, int chunk,
                                               T* G, const T* __restrict__ bra_w = nullptr, int pp_bra = -1,
-                                              int pp_ket = -1, T eps = T(0), int* work = nullptr) {
+                                              int pp_ket = -1, T eps = T(0), int* work = nullptr,
+                                              T w2 = T(0)) {
   const int LA = C.la, LB = C.lb, LC = C.lc, LD = C.ld, CK = C.ck;
   const int NB = ncart(LB), ND = ncart(LD);
   const int NAB = ncart(LA) * NB, NCD = ncart(LC) * ND;
@@ -632,9 +649,10 @@ __device__ __noinline__ void quartet_block_rt(const RtClass& C, const BasisView&
       hermite_E_rt<T>(LC, LD, kq.PAy, kq.PAy + CDy, o2q, Ecd + EC);
       hermite_E_rt<T>(LC, LD, kq.PAz, kq.PAz + CDz, o2q, Ecd + 2 * EC);
       const T r = Prec<T>::rsq(bp.p + kq.p);
-      const T alpha = bp.p * kq.p * r * r;
+      T alpha = bp.p * kq.p * r * r;
+      T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+      attenuate(w2, alpha, pref);
       prim_R_rt<T>(L, alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, bv, R);
-      const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
 #pragma unroll 1
       for (int k = 0; k < nk; ++k) {
         const int kc = kc0 + k;
@@ -992,7 +1010,7 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk(JKLaunch a) {
     decode_warp(a, (long long)base, valid ? lane : 0, bra, ket);
     if (valid) {
       int npq = 0, nbp = 0;
-      quartet_block_range<T, LA, LB, LC, LD, 0, NCD>(a.bv, bra, ket, G, (T)a.prim_eps, npq, nbp);
+      quartet_block_range<T, LA, LB, LC, LD, 0, NCD>(a.bv, bra, ket, G, (T)a.prim_eps, npq, nbp, (T)a.omega2);
       cpq += npq;
       cbp += nbp;
     }
@@ -1031,7 +1049,7 @@ __global__ void __launch_bounds__(JK_THREADS) k_jk_generic(JKLaunch a) {
       int bra, ket;
       decode_quartet(a, qi, bra, ket);
       int wk[2] = {0, 0};
-      quartet_block_rt<T, S>(C, a.bv, bra, ket, chunk, G, nullptr, -1, -1, (T)a.prim_eps, wk);
+      quartet_block_rt<T, S>(C, a.bv, bra, ket, chunk, G, nullptr, -1, -1, (T)a.prim_eps, wk, (T)a.omega2);
       if (chunk == 0) { cpq += wk[0]; cbp += wk[1]; }  // count each quartet once
       digest_rt<T>(C, a, bra, ket, chunk, G);
     }

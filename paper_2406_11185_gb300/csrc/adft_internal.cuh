@@ -111,6 +111,7 @@ struct JKLaunch {
   int* status;              // device status word
   double prim_eps;          // primitive quartets with Q_p Q_q below this are skipped
   unsigned long long* work; // [2]: primitive quartets and bra primitives evaluated, or NULL
+  double omega2;            // omega^2 of the operator erf(omega r)/r; 0 = 1/r
 };
 
 struct GradLaunch {

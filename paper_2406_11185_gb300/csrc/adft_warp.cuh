@@ -177,8 +177,9 @@ __global__ void __launch_bounds__(32 * COOP_MAX_WARPS) k_jk_warp(JKLaunch a) {
           hermite_E<T, LC, LD>(kq.PAy, kq.PAy + CD[1], o2q, Ec + EC);
           hermite_E<T, LC, LD>(kq.PAz, kq.PAz + CD[2], o2q, Ec + 2 * EC);
           const T r = Prec<T>::rsq(bp.p + kq.p);
-          const T alpha = bp.p * kq.p * r * r;
-          const T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+          T alpha = bp.p * kq.p * r * r;
+          T pref = cst<T>(4.0 * 34.98683665524972) * kq.K * r * o2p * o2q;
+          attenuate((T)a.omega2, alpha, pref);
           prim_R_scaled<T, P::L>(alpha, bp.Px - kq.Px, bp.Py - kq.Py, bp.Pz - kq.Pz, pref, bv, sl);
           // e2[cd][tau nu phi] = (-1)^(tau+nu+phi) E_x E_y E_z
           T* e2 = Ec + 3 * EC;
