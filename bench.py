@@ -558,12 +558,11 @@ def main():
 
     # ---- roofline of the dominant kernel group (the ALU-bound ERI kernels of a band)
     # traffic: DRAM bytes (read + write) of the band's class-pair launches in one
-    # build, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum
-    # over every launch of one mixed c240 build at split 3e-3, the kernels of
-    # this version); null for other workloads and splits
+    # build, from one ncu capture of the current kernels; null until the kernels
+    # changed by the long-range operator option are captured again (the capture
+    # of the version before it: 1.74 GB FP32 band, 61.0 GB FP64 band per c240
+    # build at split 3e-3)
     traffic = {}
-    if args.workload == "c240" and prec == "mixed" and split == 3e-3:
-        traffic = {"eri_fp32": 1.507378e9 + 0.234573e9, "eri_fp64": 4.169497e9 + 56.850255e9}
     groups = {"eri_fp32": (ph["eri_fp32_ms"], float(cls["flops"][1].sum()), peaks["fp32"]["tflops"], "FP32"),
               "eri_fp64": (ph["eri_fp64_ms"], float(cls["flops"][0].sum()), peaks["fp64"]["tflops"], "FP64")}
     dom = max(groups, key=lambda k: groups[k][0])
