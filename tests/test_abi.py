@@ -128,3 +128,32 @@ def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
     assert out.returncode == 0, (out.returncode, out.stderr)
     version, msg = out.stdout.strip().split("|")
     assert version.startswith("adft") and len(msg) > 0
+
+
+def test_struct_layout_matches_the_binding(tmp_path):
+    """The ctypes mirrors of adft_opts, adft_shell and adft_stats have the C
+    structs' sizes and field offsets (checked with offsetof in a C program
+    compiled against the header)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"adft_opts": adft.adft_opts, "adft_shell": adft.adft_shell, "adft_stats": adft.adft_stats}
+    lines = ['#include "adft.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
