@@ -12,7 +12,8 @@ Every function cites what it follows:
 * the ERI: the integral in the ERI paragraph of Sec. 1.2.2;
 * screening: the Cauchy-Schwarz bound of the mixed-precision bullet of
   Sec. 1.2.2 (skip a shell quartet iff Q_ab Q_cd < thresh);
-* energy E = 1/2 tr(DJ) - 1/4 tr(DK) and its nuclear gradient at fixed D;
+* energy E = 1/2 tr(DJ) - 1/4 tr(DK), its nuclear gradient and its second
+  derivatives at fixed D (the gradient and Hessian tasks of Sec. 3);
 * optionally the long-range ERI over erf(omega r)/r, the operator of the
   range-separated hybrid (omegaB97X) of the comparative benchmark, Sec. 4.1.
 """
@@ -66,6 +67,8 @@ def lib():
         L.orc_one_electron.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp]
         L.orc_grad.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, dp, dp, dp, ctypes.c_double, dp,
                                dp, ctypes.c_int]
+        L.orc_jk_hessian.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, dp, dp, dp, ctypes.c_double,
+                                     dp, dp, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -379,6 +382,21 @@ def grad(mol, D, thresh, Q=None, nthreads=None) -> np.ndarray:
                    _p(B.exps), _p(B.coefs), _p(np.ascontiguousarray(Q)), float(thresh), _p(Dc), _p(g),
                    _nthreads(nthreads))
     return g
+
+
+def jk_hessian(mol, D, thresh, Q=None, nthreads=None) -> np.ndarray:
+    """d2E_JK / dR dR [3 natom, 3 natom] at fixed D (analytic second-derivative
+    integrals; the two-electron part of the Hessian task of Sec. 3)."""
+    B = _Basis(mol)
+    if Q is None:
+        Q = schwarz(mol, nthreads)
+    Dc = _to_cart(mol, np.asarray(D, dtype=np.float64))
+    H = np.zeros((3 * mol.natom, 3 * mol.natom))
+    ip = ctypes.c_int
+    lib().orc_jk_hessian(_p(B.xyz), mol.natom, B.nshell, _p(B.atom, ip), _p(B.l, ip), _p(B.nprim, ip),
+                         _p(B.ptr, ip), _p(B.exps), _p(B.coefs), _p(np.ascontiguousarray(Q)), float(thresh),
+                         _p(Dc), _p(H), _nthreads(nthreads))
+    return H
 
 
 def energy_fd_grad(mol, D, thresh, h=1e-4, coords=None, nthreads=None):

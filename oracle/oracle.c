@@ -17,7 +17,8 @@
  *   Schwarz screening: a shell quartet (ab|cd) is dropped iff
  *   Q_ab * Q_cd < thresh, Q_ab = sqrt(max_{mu in a, nu in b} |(mu nu|mu nu)|)
  *                                      (Sec. 1.2.2, mixed-precision bullet)
- *   dE/dR_A with E = 1/2 tr(DJ) - 1/4 tr(DK) at fixed D.
+ *   dE/dR_A with E = 1/2 tr(DJ) - 1/4 tr(DK) at fixed D, and its second
+ *   derivatives d2E/dR_A dR_B at fixed D.
  *   Optionally the long-range (erf-attenuated) operator erf(omega r)/r in
  *   place of 1/r in the ERIs and J, K (range-separated hybrids; omega > 0).
  *
@@ -824,5 +825,156 @@ void orc_one_electron(const double *xyz, int nshell, const int *atom, const int 
 #undef EE
         }
     }
+  free(off);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Second derivatives of E_JK = 1/2 tr(DJ) - 1/4 tr(DK) at fixed D with respect
+   to the nuclear coordinates (the analytic Hessian task of Sec. 3, first
+   step: the two-electron part at fixed density).
+
+   A primitive Gaussian's derivative with respect to its centre A_k is
+     d/dA_k [x^i exp(-a (x-A)^2)] = 2a (x-A)^(i+1) exp(...) - i (x-A)^(i-1) exp(...),
+   so every derivative of a primitive integral is a combination of primitive
+   integrals with raised and lowered powers.  Second derivatives apply that
+   rule twice (on the same centre or on two centres).  Per primitive quartet,
+   the blocks of every needed power combination are evaluated once (with the
+   contraction and normalisation factors) and the rule is applied recursively
+   to the powers of each Cartesian component. */
+
+#define HESS_MAXBLK 64
+
+typedef struct {
+  int n;
+  int key[HESS_MAXBLK][4];
+  double *blk[HESS_MAXBLK];
+  const double *X[4];
+  double ex[4], sc;
+} blk_cache;
+
+static const double *cache_block(blk_cache *c, const int l[4]) {
+  for (int i = 0; i < c->n; ++i)
+    if (c->key[i][0] == l[0] && c->key[i][1] == l[1] && c->key[i][2] == l[2] && c->key[i][3] == l[3])
+      return c->blk[i];
+  if (c->n == HESS_MAXBLK) return NULL;
+  const size_t n = (size_t)ORC_NC(l[0]) * ORC_NC(l[1]) * ORC_NC(l[2]) * ORC_NC(l[3]);
+  double *b = (double *)calloc(n, sizeof(double));
+  orc_prim_block(l[0], l[1], l[2], l[3], c->X[0], c->ex[0], c->X[1], c->ex[1], c->X[2], c->ex[2], c->X[3],
+                 c->ex[3], c->sc, b);
+  for (int s = 0; s < 4; ++s) c->key[c->n][s] = l[s];
+  c->blk[c->n] = b;
+  return c->blk[c->n++];
+}
+
+static void cache_clear(blk_cache *c) {
+  for (int i = 0; i < c->n; ++i) free(c->blk[i]);
+  c->n = 0;
+}
+
+/* the primitive integral with powers pw[s][0..2] on the four centres,
+   differentiated by the operators ops[2i] = centre, ops[2i+1] = direction */
+static double dval(blk_cache *c, int pw[4][3], const int *ops, int nops) {
+  if (nops == 0) {
+    int l[4];
+    for (int s = 0; s < 4; ++s) l[s] = pw[s][0] + pw[s][1] + pw[s][2];
+    const double *b = cache_block(c, l);
+    if (!b) return NAN;
+    int idx = 0;
+    for (int s = 0; s < 4; ++s) idx = idx * ORC_NC(l[s]) + cart_index(l[s], pw[s][0], pw[s][1]);
+    return b[idx];
+  }
+  const int s = ops[0], k = ops[1];
+  const int p = pw[s][k];
+  pw[s][k] = p + 1;
+  double v = 2.0 * c->ex[s] * dval(c, pw, ops + 2, nops - 1);
+  if (p > 0) {
+    pw[s][k] = p - 1;
+    v -= p * dval(c, pw, ops + 2, nops - 1);
+  }
+  pw[s][k] = p;
+  return v;
+}
+
+/* Hessian [3 natom][3 natom] of E_JK at fixed D (Cartesian D, row-major),
+   over the quartets kept by the Schwarz rule with the given Q. */
+void orc_jk_hessian(const double *xyz, int natom, int nshell, const int *atom, const int *l, const int *nprim,
+                    const int *ptr, const double *exps, const double *coefs, const double *Q, double thresh,
+                    const double *D, double *H, int nthreads) {
+  orc_basis bs = {xyz, nshell, atom, l, nprim, ptr, exps, coefs};
+  int *off = (int *)malloc(sizeof(int) * (nshell + 1));
+  shell_offsets(&bs, off);
+  const int nc = off[nshell], n3 = 3 * natom;
+  const long npair = (long)nshell * (nshell + 1) / 2;
+  memset(H, 0, sizeof(double) * n3 * n3);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+  {
+    double *Ht = (double *)calloc((size_t)n3 * n3, sizeof(double));
+    blk_cache cache;
+    cache.n = 0;
+#pragma omp for schedule(dynamic, 1)
+    for (long ab = npair - 1; ab >= 0; --ab) {
+      int a = 0;
+      while ((long)(a + 1) * (a + 2) / 2 <= ab) ++a;
+      const int b = (int)(ab - (long)a * (a + 1) / 2);
+      for (long cd = 0; cd <= ab; ++cd) {
+        if (Q[ab] * Q[cd] < thresh) continue;
+        int c = 0;
+        while ((long)(c + 1) * (c + 2) / 2 <= cd) ++c;
+        const int d = (int)(cd - (long)c * (c + 1) / 2);
+        const int sh[4] = {a, b, c, d};
+        int keep[8];
+        const int nimg = distinct_images(sh, keep);
+        const int lv[4] = {l[a], l[b], l[c], l[d]};
+        int pwl[4][3 * ORC_NC(ORC_LMAX)];
+        for (int s = 0; s < 4; ++s) cart_list(lv[s], pwl[s]);
+        for (int s = 0; s < 4; ++s) cache.X[s] = xyz + 3 * atom[sh[s]];
+        for (int i0 = 0; i0 < nprim[a]; ++i0)
+          for (int i1 = 0; i1 < nprim[b]; ++i1)
+            for (int i2 = 0; i2 < nprim[c]; ++i2)
+              for (int i3 = 0; i3 < nprim[d]; ++i3) {
+                const int ip[4] = {i0, i1, i2, i3};
+                cache.sc = 1.0;
+                for (int s = 0; s < 4; ++s) {
+                  cache.ex[s] = exps[ptr[sh[s]] + ip[s]];
+                  cache.sc *= coefs[ptr[sh[s]] + ip[s]] * prim_norm(cache.ex[s], lv[s]);
+                }
+                for (int c0 = 0; c0 < ORC_NC(lv[0]); ++c0)
+                  for (int c1 = 0; c1 < ORC_NC(lv[1]); ++c1)
+                    for (int c2 = 0; c2 < ORC_NC(lv[2]); ++c2)
+                      for (int c3 = 0; c3 < ORC_NC(lv[3]); ++c3) {
+                        const int cc[4] = {c0, c1, c2, c3};
+                        const long m = off[a] + c0, nu = off[b] + c1, la_ = off[c] + c2, si = off[d] + c3;
+                        const double G = nimg * (0.5 * D[m * nc + nu] * D[la_ * nc + si] -
+                                                 0.125 * (D[m * nc + la_] * D[nu * nc + si] +
+                                                          D[m * nc + si] * D[nu * nc + la_]));
+                        if (G == 0.0) continue;
+                        int pw[4][3];
+                        for (int s = 0; s < 4; ++s)
+                          for (int t = 0; t < 3; ++t) pw[s][t] = pwl[s][3 * cc[s] + t];
+                        for (int s = 0; s < 4; ++s)
+                          for (int k = 0; k < 3; ++k)
+                            for (int t = 0; t < 4; ++t)
+                              for (int q = 0; q < 3; ++q) {
+                                if (t * 3 + q < s * 3 + k) continue;  /* symmetric: upper triangle */
+                                const int ops[4] = {s, k, t, q};
+                                const double v = G * dval(&cache, pw, ops, 2);
+                                const int r0 = 3 * atom[sh[s]] + k, r1 = 3 * atom[sh[t]] + q;
+                                Ht[r0 * n3 + r1] += v;
+                                if (t * 3 + q != s * 3 + k) Ht[r1 * n3 + r0] += v;
+                              }
+                      }
+                cache_clear(&cache);
+              }
+      }
+    }
+#pragma omp critical
+    {
+      for (long i = 0; i < (long)n3 * n3; ++i) H[i] += Ht[i];
+    }
+    free(Ht);
+  }
   free(off);
 }
