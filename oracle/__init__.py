@@ -67,6 +67,7 @@ def lib():
         L.orc_one_electron.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp]
         L.orc_grad.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, dp, dp, dp, ctypes.c_double, dp,
                                dp, ctypes.c_int]
+        L.orc_one_electron_grad.argtypes = basis + [ctypes.c_int, dp, dp, dp, dp]
         L.orc_jk_hessian.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, ip, ip, ip, dp, dp, dp, ctypes.c_double,
                                      dp, dp, ctypes.c_int]
         _lib = L
@@ -492,3 +493,28 @@ def scf(mol, charges, nocc, thresh, max_iter=100, e_tol=1e-10, g_tol=1e-8, diis_
             F = sum(ci * Fi for ci, Fi in zip(c, focks))
         D = density(F)
     return dict(energy=E, D=D, iterations=max_iter, converged=False, F=F, S=S, H=H, e_nuc=e_nuc)
+
+
+def scf_gradient(mol, charges, nocc, thresh, Q=None, nthreads=None, **scf_kw):
+    """Nuclear gradient [natom, 3] of the converged closed-shell SCF energy
+    (the single-point force task of Sec. 3, around the J/K gradient):
+
+        dE/dR = sum D dH/dR - sum W dS/dR + dE_JK/dR|_D + dE_nuc/dR,
+        W = 1/2 D F D (the energy-weighted density of the converged orbitals).
+
+    Returns (energy, gradient, the scf() result)."""
+    r = scf(mol, charges, nocc, thresh, **scf_kw)
+    D, F = r["D"], r["F"]
+    W = 0.5 * D @ F @ D
+    B = _Basis(mol)
+    q = np.ascontiguousarray(np.asarray(charges, dtype=np.float64))
+    g = np.zeros((mol.natom, 3))
+    lib().orc_one_electron_grad(*B.args(), mol.natom, _p(q), _p(_to_cart(mol, D)), _p(_to_cart(mol, W)), _p(g))
+    g += grad(mol, D, thresh, Q=Q, nthreads=nthreads)
+    X = np.asarray(mol.atoms, dtype=np.float64)
+    for a in range(mol.natom):
+        for b in range(mol.natom):
+            if a != b:
+                d = X[a] - X[b]
+                g[a] -= q[a] * q[b] * d / np.linalg.norm(d) ** 3
+    return r["energy"], g, r

@@ -18,7 +18,8 @@
  *   Q_ab * Q_cd < thresh, Q_ab = sqrt(max_{mu in a, nu in b} |(mu nu|mu nu)|)
  *                                      (Sec. 1.2.2, mixed-precision bullet)
  *   dE/dR_A with E = 1/2 tr(DJ) - 1/4 tr(DK) at fixed D, and its second
- *   derivatives d2E/dR_A dR_B at fixed D.
+ *   derivatives d2E/dR_A dR_B at fixed D; the one-electron part of the
+ *   closed-shell SCF force.
  *   Optionally the long-range (erf-attenuated) operator erf(omega r)/r in
  *   place of 1/r in the ERIs and J, K (range-separated hybrids; omega > 0).
  *
@@ -976,5 +977,113 @@ void orc_jk_hessian(const double *xyz, int natom, int nshell, const int *atom, c
     }
     free(Ht);
   }
+  free(off);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nuclear gradient of the one-electron part of the closed-shell SCF energy
+   (the single-point force task of Sec. 3 around the J/K gradient):
+     sum_{mu nu} D_mu,nu dH_mu,nu/dR - sum_{mu nu} W_mu,nu dS_mu,nu/dR,
+   W the energy-weighted density.  Derivatives with respect to the centres of
+   the two functions by the raise/lower rule of the Hessian section; the
+   derivative of a nuclear-attraction integral with respect to its nucleus C
+   by translational invariance, d/dC = -(d/dA + d/dB) for that nucleus's term.
+   Matrices are Cartesian [nc][nc] row-major; grad is [natom][3] (added to). */
+
+/* S, T and the attraction to a unit positive charge at C (V = -2pi/p sum E E E R)
+   of two unnormalised primitive Cartesian Gaussians with powers ia at A
+   (exponent a) and ib at B (exponent b) */
+static void prim_one_elem(const int ia[3], const double *A, double a, const int ib[3], const double *B, double b,
+                          const double *C, double *s, double *t, double *v) {
+  const double p = a + b;
+  double E[3][(ORC_LMAX + 3) * (ORC_LMAX + 5) * (2 * ORC_LMAX + 8)];
+  int jm[3], nt[3];
+  for (int k = 0; k < 3; ++k) {
+    jm[k] = ib[k] + 2;
+    nt[k] = ia[k] + jm[k] + 1;
+    hermite_e(ia[k], jm[k], a, b, A[k], B[k], E[k]);
+  }
+#define EO(k, ii, jj, tt) E[k][((ii) * (jm[k] + 1) + (jj)) * nt[k] + (tt)]
+  const double sq = sqrt((double)ORC_PI / p);
+  double s1[3], t1[3];
+  for (int k = 0; k < 3; ++k) {
+    const int ii = ia[k], jj = ib[k];
+    s1[k] = EO(k, ii, jj, 0) * sq;
+    const double sm2 = jj >= 2 ? EO(k, ii, jj - 2, 0) * sq : 0.0;
+    const double sp2 = EO(k, ii, jj + 2, 0) * sq;
+    t1[k] = -0.5 * (jj * (jj - 1) * sm2 - 2.0 * b * (2 * jj + 1) * s1[k] + 4.0 * b * b * sp2);
+  }
+  *s = s1[0] * s1[1] * s1[2];
+  *t = t1[0] * s1[1] * s1[2] + s1[0] * t1[1] * s1[2] + s1[0] * s1[1] * t1[2];
+  const int L = ia[0] + ib[0] + ia[1] + ib[1] + ia[2] + ib[2];
+  double R[(2 * ORC_LMAX + 3) * (2 * ORC_LMAX + 3) * (2 * ORC_LMAX + 3)];
+  double P[3];
+  for (int k = 0; k < 3; ++k) P[k] = (a * A[k] + b * B[k]) / p;
+  hermite_r(L, p, P[0] - C[0], P[1] - C[1], P[2] - C[2], R);
+  double acc = 0.0;
+  for (int tt = 0; tt <= ia[0] + ib[0]; ++tt)
+    for (int u = 0; u <= ia[1] + ib[1]; ++u)
+      for (int w = 0; w <= ia[2] + ib[2]; ++w) acc += EO(0, ia[0], ib[0], tt) * EO(1, ia[1], ib[1], u) *
+                                                          EO(2, ia[2], ib[2], w) * R[RIDX(tt, u, w)];
+  *v = -2.0 * (double)ORC_PI / p * acc;
+#undef EO
+}
+
+void orc_one_electron_grad(const double *xyz, int nshell, const int *atom, const int *l, const int *nprim,
+                           const int *ptr, const double *exps, const double *coefs, int natom,
+                           const double *charges, const double *D, const double *W, double *grad) {
+  orc_basis bs = {xyz, nshell, atom, l, nprim, ptr, exps, coefs};
+  int *off = (int *)malloc(sizeof(int) * (nshell + 1));
+  double *dvc = (double *)malloc(sizeof(double) * (natom > 0 ? natom : 1));
+  shell_offsets(&bs, off);
+  const int nc = off[nshell];
+  for (int sa = 0; sa < nshell; ++sa)
+    for (int sb = 0; sb < nshell; ++sb) {
+      const int la = l[sa], lb = l[sb];
+      const double *A = xyz + 3 * atom[sa], *B = xyz + 3 * atom[sb];
+      int pa[3 * ORC_NC(ORC_LMAX)], pb[3 * ORC_NC(ORC_LMAX)];
+      cart_list(la, pa);
+      cart_list(lb, pb);
+      for (int i = 0; i < nprim[sa]; ++i)
+        for (int j = 0; j < nprim[sb]; ++j) {
+          const double a = exps[ptr[sa] + i], b = exps[ptr[sb] + j];
+          const double cc = coefs[ptr[sa] + i] * prim_norm(a, la) * coefs[ptr[sb] + j] * prim_norm(b, lb);
+          for (int ia = 0; ia < ORC_NC(la); ++ia)
+            for (int ib = 0; ib < ORC_NC(lb); ++ib) {
+              const long o = (long)(off[sa] + ia) * nc + off[sb] + ib;
+              const double dw = D[o], ww = W[o];
+              for (int side = 0; side < 2; ++side)  /* 0: centre A (bra), 1: centre B (ket) */
+                for (int k = 0; k < 3; ++k) {
+                  int pw_a[3], pw_b[3];
+                  for (int q = 0; q < 3; ++q) { pw_a[q] = pa[3 * ia + q]; pw_b[q] = pb[3 * ib + q]; }
+                  int *pw = side == 0 ? pw_a : pw_b;
+                  const double ex = side == 0 ? a : b;
+                  const int p0 = pw[k];
+                  double ds = 0.0, dt = 0.0;
+                  for (int c = 0; c < natom; ++c) dvc[c] = 0.0;
+                  for (int term = 0; term < 2; ++term) {
+                    double f;
+                    if (term == 0) { pw[k] = p0 + 1; f = 2.0 * ex; }
+                    else { if (p0 == 0) break; pw[k] = p0 - 1; f = -(double)p0; }
+                    double s, t, v;
+                    for (int c = 0; c < natom; ++c) {
+                      prim_one_elem(pw_a, A, a, pw_b, B, b, xyz + 3 * c, &s, &t, &v);
+                      dvc[c] += f * charges[c] * v;
+                    }
+                    ds += f * s;
+                    dt += f * t;
+                    pw[k] = p0;
+                  }
+                  double dv = 0.0;
+                  for (int c = 0; c < natom; ++c) dv += dvc[c];
+                  const int ca = side == 0 ? atom[sa] : atom[sb];
+                  grad[3 * ca + k] += cc * (dw * (dt + dv) - ww * ds);
+                  /* the nucleus of each attraction term moves against both centres */
+                  for (int c = 0; c < natom; ++c) grad[3 * c + k] -= cc * dw * dvc[c];
+                }
+            }
+        }
+    }
+  free(dvc);
   free(off);
 }
