@@ -188,6 +188,20 @@ int adft_jk_grad(adft_basis* b, const double* D, const adft_opts* opts, double* 
  *   the call returns). */
 int adft_one_electron(adft_basis* b, const double* charges, void* stream, double* S, double* T, double* V);
 
+/* Nuclear gradient of the one-electron part of the closed-shell SCF energy
+ * (the single-point force task, Sec. 3, around adft_jk_grad):
+ *   grad = sum D dH/dR - sum W dS/dR,  H = T + V as in adft_one_electron,
+ * W the energy-weighted density (1/2 D F D at convergence).  The caller adds
+ * adft_jk_grad (at the same D) and the nuclear repulsion gradient.
+ *   charges: host [natom].  D, W: dev [nbf][nbf] in the basis's output
+ *   functions, symmetric.  grad: dev [natom][3], overwritten.
+ * Enqueued on stream (NULL = legacy default stream); no synchronisation.
+ * Uses the handle's Cartesian D and J workspaces (do not overlap with a
+ * build of the same handle on another stream).  Single-molecule bases only
+ * (ADFT_ERR_ARG otherwise). */
+int adft_one_electron_grad(adft_basis* b, const double* charges, const double* D, const double* W, void* stream,
+                           double* grad);
+
 /* Statistics of the last adft_jk_build / adft_jk_energy / adft_jk_grad on
  * this handle (synchronises the handle's last stream). */
 int adft_jk_last_stats(adft_basis* b, adft_stats* st);

@@ -495,6 +495,17 @@ def scf(mol, charges, nocc, thresh, max_iter=100, e_tol=1e-10, g_tol=1e-8, diis_
     return dict(energy=E, D=D, iterations=max_iter, converged=False, F=F, S=S, H=H, e_nuc=e_nuc)
 
 
+def one_electron_grad(mol, charges, D, W) -> np.ndarray:
+    """sum D dH/dR - sum W dS/dR [natom, 3] for D and W in the molecule's
+    output basis (the one-electron part of the closed-shell SCF gradient)."""
+    B = _Basis(mol)
+    q = np.ascontiguousarray(np.asarray(charges, dtype=np.float64))
+    g = np.zeros((mol.natom, 3))
+    lib().orc_one_electron_grad(*B.args(), mol.natom, _p(q), _p(_to_cart(mol, np.asarray(D, dtype=np.float64))),
+                                _p(_to_cart(mol, np.asarray(W, dtype=np.float64))), _p(g))
+    return g
+
+
 def scf_gradient(mol, charges, nocc, thresh, Q=None, nthreads=None, **scf_kw):
     """Nuclear gradient [natom, 3] of the converged closed-shell SCF energy
     (the single-point force task of Sec. 3, around the J/K gradient):
@@ -506,10 +517,8 @@ def scf_gradient(mol, charges, nocc, thresh, Q=None, nthreads=None, **scf_kw):
     r = scf(mol, charges, nocc, thresh, **scf_kw)
     D, F = r["D"], r["F"]
     W = 0.5 * D @ F @ D
-    B = _Basis(mol)
     q = np.ascontiguousarray(np.asarray(charges, dtype=np.float64))
-    g = np.zeros((mol.natom, 3))
-    lib().orc_one_electron_grad(*B.args(), mol.natom, _p(q), _p(_to_cart(mol, D)), _p(_to_cart(mol, W)), _p(g))
+    g = one_electron_grad(mol, q, D, W)
     g += grad(mol, D, thresh, Q=Q, nthreads=nthreads)
     X = np.asarray(mol.atoms, dtype=np.float64)
     for a in range(mol.natom):

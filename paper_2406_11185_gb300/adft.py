@@ -35,7 +35,7 @@ EXPORTED = [
     "adft_basis_destroy", "adft_batch_create", "adft_batch_offsets", "adft_batch_grad_offsets", "adft_batch_jk",
     "adft_batch_destroy", "adft_status_string", "adft_last_error_message", "adft_version", "adft_autotune",
     "adft_set_tuning", "adft_jk_plan", "adft_energy_static", "adft_batch_last_stats", "adft_batch_last_timings", "adft_batch_autotune",
-    "adft_batch_set_tuning", "adft_alu_peak", "adft_jk_last_class_stats", "adft_one_electron",
+    "adft_batch_set_tuning", "adft_alu_peak", "adft_jk_last_class_stats", "adft_one_electron", "adft_one_electron_grad",
 ]
 
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.adft_jk_last_class_stats.argtypes = [vp, i64p, i64p, i64p, dp]
     L.adft_one_electron.argtypes = [vp, dp, vp, vp, vp, vp]
+    L.adft_one_electron_grad.argtypes = [vp, dp, vp, vp, vp, vp]
     L.adft_status_string.argtypes = [ip]
     L.adft_status_string.restype = ctypes.c_char_p
     L.adft_last_error_message.restype = ctypes.c_char_p
@@ -331,6 +332,24 @@ def adft_one_electron(basis: Basis, charges, stream=None, device=None):
     _check(load().adft_one_electron(basis.handle, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     _stream_ptr(stream), *[vp(t.data_ptr()) for t in out]), "adft_one_electron")
     return tuple(out)
+
+
+def adft_one_electron_grad(basis: Basis, charges, D, W, stream=None):
+    """sum D dH/dR - sum W dS/dR [natom, 3] (CUDA float64) for the density D
+    and the energy-weighted density W (CUDA [nbf, nbf] on the current device):
+    the one-electron part of the closed-shell SCF nuclear gradient."""
+    import torch
+    q = np.ascontiguousarray(np.asarray(charges, dtype=np.float64))
+    if q.shape != (basis.natom,):
+        raise ValueError(f"charges must hold {basis.natom} values")
+    _check_matrix(D, basis.nbf)
+    _check_matrix(W, basis.nbf)
+    g = torch.empty((basis.natom, 3), dtype=torch.float64, device=D.device)
+    vp = ctypes.c_void_p
+    _check(load().adft_one_electron_grad(basis.handle, q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         vp(D.data_ptr()), vp(W.data_ptr()), _stream_ptr(stream),
+                                         vp(g.data_ptr())), "adft_one_electron_grad")
+    return g
 
 
 def adft_jk_last_class_stats(basis: Basis) -> dict:

@@ -1359,6 +1359,31 @@ int adft_one_electron(adft_basis* b, const double* charges, void* stream, double
   return ADFT_OK;
 }
 
+int adft_one_electron_grad(adft_basis* b, const double* charges, const double* D, const double* W, void* stream,
+                           double* grad) {
+  if (!b || !charges || !D || !W || !grad) { set_error("NULL argument"); return ADFT_ERR_ARG; }
+  if (b->nmol != 1) { set_error("one-electron gradients are computed for single-molecule bases"); return ADFT_ERR_ARG; }
+  for (int i = 0; i < b->natom; ++i)
+    if (!isfinite(charges[i])) { set_error("charges must be finite"); return ADFT_ERR_ARG; }
+  int st = set_device(b);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& w = b->ws;
+  const long long nc2 = b->mol_cbase[b->nmol];
+  const XformArgs x = xform_args(b);
+  ADFT_CUDA(cudaMemcpyAsync(w.charges, charges, sizeof(double) * b->natom, cudaMemcpyHostToDevice, s));
+  // D and W to Cartesian (the FP32 copy is scratch here; every build rewrites it)
+  k_d_to_cart<<<(unsigned)((nc2 + 255) / 256), 256, 0, s>>>(x, nc2, D, w.Dc, w.Dc32);
+  ADFT_CUDA(cudaGetLastError());
+  k_d_to_cart<<<(unsigned)((nc2 + 255) / 256), 256, 0, s>>>(x, nc2, W, w.Jc, w.Dc32);
+  ADFT_CUDA(cudaGetLastError());
+  ADFT_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * 3 * b->natom, s));
+  ADFT_CUDA(launch_one_electron_grad(view(b), b->d_shell_nprim, b->d_shell_poff, b->d_exps, b->d_ncoefs, w.charges,
+                                     w.Dc, w.Jc, grad, s));
+  b->last_stream = s;
+  return ADFT_OK;
+}
+
 int adft_jk_last_class_stats(adft_basis* b, int64_t* quartets, int64_t* prim_quartets, int64_t* bra_prims,
                              double* flops) {
   if (!b) { set_error("NULL basis"); return ADFT_ERR_ARG; }

@@ -150,6 +150,9 @@ cudaError_t launch_prim_schwarz(int X, const BasisView& bv, int first, int n, co
 cudaError_t launch_one_electron(const BasisView& bv, const int* shell_nprim, const int* shell_poff,
                                 const double* exps, const double* ncoefs, const double* charges, double* S,
                                 double* T, double* V, cudaStream_t s);
+cudaError_t launch_one_electron_grad(const BasisView& bv, const int* shell_nprim, const int* shell_poff,
+                                     const double* exps, const double* ncoefs, const double* charges,
+                                     const double* Dc, const double* Wc, double* grad, cudaStream_t s);
 // Primitive pairs whose bound Qp * max(Qp) is at or below this are dropped at
 // basis creation (1e-3 of the paper's default tolerance 1e-12).
 constexpr double PRIM_EPS = 1e-15;

@@ -121,6 +121,34 @@ class RHF:
         return dict(energy=E, D=D, iterations=max_iter, converged=False, builds=builds, gradient_norm=gnorm)
 
 
+def nuclear_repulsion_gradient(atoms, charges) -> np.ndarray:
+    """d/dR_A sum_{A<B} Z_A Z_B / |R_A - R_B|, [natom, 3]."""
+    X = np.asarray(atoms, dtype=np.float64)
+    Z = np.asarray(charges, dtype=np.float64)
+    d = X[:, None, :] - X[None, :, :]
+    r = np.linalg.norm(d, axis=-1)
+    np.fill_diagonal(r, np.inf)
+    return -np.sum((Z[:, None] * Z[None, :] / r ** 3)[..., None] * d, axis=1)
+
+
+def scf_gradient(rhf: RHF, result: dict):
+    """Nuclear gradient [natom, 3] (CUDA float64) of a converged RHF energy,
+    the single-point force task: sum D dH/dR - sum W dS/dR with
+    W = 1/2 D F D (adft_one_electron_grad), plus dE_JK/dR at fixed D
+    (adft_jk_grad, F = H + J - 1/2 K so E_JK = 1/2 tr(DJ) - 1/4 tr(DK)), plus
+    the nuclear repulsion gradient."""
+    torch = rhf.torch
+    D = result["D"]
+    J, K = rhf._jk(D, rhf.thresh, rhf.split)
+    F = rhf.H + J - 0.5 * K
+    W = 0.5 * (D @ F @ D)
+    W = 0.5 * (W + W.T)
+    g = adft.adft_one_electron_grad(rhf.basis, rhf.charges, D, W, stream=rhf.stream)
+    g = g + adft.adft_jk_grad(rhf.basis, D, thresh=rhf.thresh, split=rhf.split, precision=rhf.precision, check=False,
+                              stream=rhf.stream)
+    return g + torch.as_tensor(nuclear_repulsion_gradient(rhf.mol.atoms, rhf.charges), device=g.device)
+
+
 def run_scf(mol, **kw) -> dict:
     """RHF(mol, **options).run() with a wall-clock time added."""
     t = time.time()

@@ -64,3 +64,37 @@ def test_scf_mixed_precision_energy():
     print(f"small mixed: dE={r['energy'] - ref['energy']:.2e} iterations {r['iterations']}")
     assert r["converged"]
     assert abs(r["energy"] - ref["energy"]) <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["tiny", "small_f3"])
+def test_one_electron_gradient_vs_oracle(name):
+    """sum D dH/dR - sum W dS/dR on the GPU against oracle.one_electron_grad
+    for a synthetic D and a symmetric W (s to f shells)."""
+    mol, opt = synth.config(name)
+    Z = synth.nuclear_charges(mol)
+    D = synth.make_density(mol, synth.default_nocc(mol, opt["nocc"]), opt["dseed"])
+    rng = np.random.default_rng(7)
+    W = rng.normal(size=D.shape)
+    W = 0.5 * (W + W.T)
+    b = adft.Basis.from_molecule(mol)
+    g = adft.adft_one_electron_grad(b, Z, torch.from_numpy(D).cuda(), torch.from_numpy(W).cuda()).cpu().numpy()
+    ref = oracle.one_electron_grad(mol, Z, D, W)
+    err = np.max(np.abs(g - ref))
+    print(f"{name}: max|d grad_1e|={err:.2e} max={np.max(np.abs(ref)):.2e}")
+    assert err <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_scf_force_vs_oracle():
+    """The single-point force of a converged FP64 SCF (one-electron gradient,
+    J/K gradient at fixed D, nuclear repulsion) against oracle.scf_gradient."""
+    mol = synth.make_molecule(1801, 1, 2, "3s2p1d", "2s1p", (1, 2), (0.1, 5e3), (1.4, 2.0), True, "force")
+    Z = synth.nuclear_charges(mol)
+    nocc = int(round(Z.sum())) // 2
+    rhf = scf.RHF(mol, nocc=nocc, thresh=1e-12, precision="fp64", incremental=False)
+    r = rhf.run(e_tol=1e-12, g_tol=1e-10)
+    g = scf.scf_gradient(rhf, r).cpu().numpy()
+    E_ref, g_ref, _ = oracle.scf_gradient(mol, Z, nocc, 1e-12, e_tol=1e-12, g_tol=1e-10)
+    print(f"force: dE={r['energy'] - E_ref:.2e} max|dg|={np.max(np.abs(g - g_ref)):.2e}")
+    assert r["converged"] and abs(r["energy"] - E_ref) <= 1e-9
+    assert np.max(np.abs(g - g_ref)) <= 1e-7
+    assert np.max(np.abs(g.sum(axis=0))) <= 1e-9
