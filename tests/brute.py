@@ -44,8 +44,10 @@ def _pair_integrals(t, la, lb, lc, ld, A, B, C, D, a, b, c, d):
     return out
 
 
-def prim_block(ls, centres, exps):
-    """Unnormalised primitive [ab|cd] for all Cartesian components."""
+def prim_block(ls, centres, exps, omega=None):
+    """Unnormalised primitive [ab|cd] for all Cartesian components; with
+    omega, over erf(omega r12)/r12 = (2/sqrt(pi)) int_0^omega exp(-t^2 r12^2) dt
+    (the same t-integral stopped at t = omega)."""
     la, lb, lc, ld = ls
     A, B, C, D = (np.asarray(x, dtype=float) for x in centres)
     a, b, c, d = exps
@@ -67,7 +69,8 @@ def prim_block(ls, centres, exps):
                         vals[i, j, k, m] = v
         return vals.ravel() * (2.0 / math.sqrt(math.pi)) / (1.0 - u) ** 2
 
-    res, err = quad_vec(f, 0.0, 1.0, epsabs=1e-16, epsrel=1e-13, limit=400)
+    u_max = 1.0 if omega is None else omega / (1.0 + omega)
+    res, err = quad_vec(f, 0.0, u_max, epsabs=1e-16, epsrel=1e-13, limit=400)
     return res.reshape(len(ca), len(cb), len(cc), len(cd))
 
 

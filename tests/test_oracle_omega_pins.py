@@ -7,6 +7,8 @@ against something other than the oracle's own formula:
   integrand has a closed form, integrated by Gauss-Legendre quadrature;
 * (p s|s s) and (d s|s s) against central differences of that (ss|ss) in the
   centre A (d/dA_x of exp(-a (x-A_x)^2) = 2a (x-A_x) exp(...));
+* every Cartesian component of p to f blocks against the brute-force
+  quadrature of tests/brute.py with its t-integral stopped at t = omega;
 * the limits: omega -> infinity gives the Coulomb integral, omega -> 0 gives
   2 omega / sqrt(pi) times the product of the two overlap distributions;
 * J of the attenuated operator: symmetric, and for a closed-shell density
@@ -20,6 +22,8 @@ import pytest
 
 import oracle
 from paper_2406_11185_gb300 import synth
+
+from . import brute
 
 
 def _ss_geminal(centres, exps, omega, n=80):
@@ -100,3 +104,14 @@ def test_attenuated_coulomb_energy_is_positive_and_below_coulomb():
     Ji, Ki = oracle.jk(mol, D, opt["thresh"], omega=1e7)
     assert np.max(np.abs(Ji - J)) <= 1e-9 * np.max(np.abs(J))
     assert np.max(np.abs(Ki - K)) <= 1e-9 * np.max(np.abs(K))
+
+
+@pytest.mark.parametrize("ls,omega", [((1, 1, 0, 0), 0.5), ((2, 1, 1, 0), 0.3), ((2, 2, 1, 1), 1.2),
+                                      ((3, 0, 1, 0), 0.7)])
+def test_blocks_match_brute_force(ls, omega):
+    rng = np.random.default_rng(sum((i + 5) * l for i, l in enumerate(ls)) + 29)
+    cen = [rng.normal(size=3) * 0.9 for _ in range(4)]
+    ex = list(np.exp(rng.uniform(np.log(0.15), np.log(6.0), size=4)))
+    ref = brute.prim_block(ls, cen, ex, omega=omega)
+    got = oracle.prim_block(ls, cen, ex, omega=omega)
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
