@@ -260,9 +260,15 @@ def run_scf(args):
            "nocc": int(round(float(np.sum(synth.nuclear_charges(mol))))) // 2, "thresh": opt["thresh"], "runs": []}
     for prec, inc in (("fp64", False), ("fp64", True), ("mixed", True)):
         t0 = time.time()
-        r = scf.RHF(mol, thresh=opt["thresh"], precision=prec, split=split, incremental=inc).run(e_tol=1e-9,
-                                                                                              g_tol=1e-6)
+        rhf = scf.RHF(mol, thresh=opt["thresh"], precision=prec, split=split, incremental=inc)
+        r = rhf.run(e_tol=1e-9, g_tol=1e-6)
         torch.cuda.synchronize()
+        # the single-point force of the converged density (one-electron, J/K
+        # and nuclear-repulsion gradients)
+        tf = time.time()
+        g = scf.scf_gradient(rhf, r)
+        torch.cuda.synchronize()
+        force_s = time.time() - tf
         full = [ms for k, ms in r["builds"] if k == "full"]
         inc_ms = [ms for k, ms in r["builds"] if k == "incremental"]
         out["runs"].append({"precision": prec, "split": split if prec == "mixed" else None, "incremental": inc,
@@ -271,7 +277,9 @@ def run_scf(args):
                             "full_build_ms_median": float(np.median(full)) if full else None,
                             "incremental_builds": len(inc_ms),
                             "incremental_build_ms_median": float(np.median(inc_ms)) if inc_ms else None,
-                            "jk_ms_total": float(sum(full) + sum(inc_ms))})
+                            "jk_ms_total": float(sum(full) + sum(inc_ms)), "force_s": force_s,
+                            "force_max_abs": float(g.abs().max().item()),
+                            "net_force": float(g.sum(0).abs().max().item())})
     e64 = out["runs"][0]["energy"]
     for run in out["runs"]:
         run["energy_err_vs_full_fp64"] = abs(run["energy"] - e64)
@@ -442,7 +450,8 @@ def main():
     ap.add_argument("--probe-reps", type=int, default=2, help="with --probe: number of builds")
     ap.add_argument("--scf", action="store_true",
                     help="run the closed-shell SCF driver (scf.RHF) on the workload and print its iterations, "
-                         "energy and J/K build times (full and incremental) as one JSON line")
+                         "energy, J/K build times (full and incremental) and the single-point force as one JSON "
+                         "line")
     args = ap.parse_args()
     if args.scf:
         return run_scf(args)
